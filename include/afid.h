@@ -1,0 +1,176 @@
+/*
+ * afid.h -- C ABI of the GB300 pressure-correction library (libafid.so).
+ *
+ * The library computes the data-parallel hot path of the fractional-step
+ * solver of AFiD-GPU (Zhu et al., arXiv 1705.01423): the divergence of a
+ * staggered velocity field, a real-to-complex FFT along x and a complex FFT
+ * along y, one tridiagonal (Thomas) solve per wavenumber pair along the
+ * stretched wall-normal direction z with zero-flux walls, the inverse FFTs, the
+ * projection of the velocity and the pressure update (Sec. 2.2), and around it
+ * the explicit terms and Crank-Nicolson wall-normal sweeps of one low-storage
+ * RK3 substep (Sec. 2.1).
+ *
+ * Coordinates: x and y periodic and uniform, z bounded and stretched (the
+ * paper calls the wall-normal direction x). All field arrays are C-ordered
+ * [z][y][x] (x fastest), FP64, contiguous, resident on the CUDA device, and at
+ * least 16-byte aligned:
+ *   u, v, p, phi, rhs   [nz][ny][nx]    u on x-faces, v on y-faces, p/phi at centres
+ *   w, T                [nz+1][ny][nx]  z-faces; planes 0 and nz are the walls
+ *
+ * Ownership: the caller owns every field buffer passed in; the context owns its
+ * workspace, allocated once in afid_create and never inside a compute call.
+ *
+ * Execution: every compute call only enqueues work on the context's stream
+ * and returns; it never synchronises the device, except that a non-NULL
+ * afid_info* makes the call wait for its own work and fill the struct.
+ * Arguments are validated on the host before anything is launched; a
+ * validation error launches nothing. No call traps or spins on the device.
+ *
+ * Thread safety: one context must not be used from two host threads at once.
+ */
+#ifndef AFID_H
+#define AFID_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AFID_OK = 0,
+  AFID_ERR_INVALID_ARG = 1,      /* NULL pointer, bad index, non-positive length ...      */
+  AFID_ERR_UNSUPPORTED_SIZE = 2, /* nx, ny not a power of two in [8, 4096]; nz < 3 or > 4096 */
+  AFID_ERR_ALIGNMENT = 3,        /* a device pointer not 16-byte aligned                  */
+  AFID_ERR_NOT_CONVERGED = 4,    /* mixed refinement hit refine_max_iter (phi is the best) */
+  AFID_ERR_INCONSISTENT_RHS = 5, /* |weighted mean of rhs| > 1e-8 max|rhs| (reported only
+                                    when afid_info is requested; the mean is removed)     */
+  AFID_ERR_CUDA = 6,             /* a CUDA runtime call failed                            */
+  AFID_ERR_OOM = 7               /* workspace allocation failed in afid_create            */
+} afid_status;
+
+typedef enum {
+  AFID_FP64 = 0, /* every stage in FP64                                                  */
+  AFID_MIXED = 1 /* FP32 transforms and Thomas sweeps, FP64 lowest modes, FP64 residual
+                    iterative refinement of the Poisson solve                          */
+} afid_precision;
+
+/* flags */
+#define AFID_POISSON_ONLY 1 /* do not allocate the RK3 substep workspace */
+
+typedef struct {
+  int nx, ny, nz;          /* cells; nx, ny powers of two                            */
+  double lx, ly;           /* periodic box lengths                                   */
+  const double* zf;        /* HOST pointer, nz+1 face coordinates, strictly increasing */
+  int precision;           /* afid_precision                                         */
+  double refine_tol;       /* mixed: stop when the estimated relative error of phi
+                              is <= refine_tol (see afid_info.err_estimate)          */
+  int refine_max_iter;     /* mixed: maximum refinement iterations (>= 1)             */
+  int flags;               /* AFID_POISSON_ONLY or 0                                 */
+} afid_grid_desc;
+
+typedef struct {
+  double nu, kappa;        /* momentum and scalar diffusivities                      */
+  double buoyancy;         /* coefficient of T in the w equation                     */
+  double u_bot, u_top;     /* wall velocities along x (Couette)                      */
+  double T_bot, T_top;     /* wall temperatures                                      */
+} afid_phys;
+
+typedef struct {
+  int iters;               /* refinement iterations used (1 for AFID_FP64)           */
+  double rel_residual;     /* mixed: final ||r||_2/||b||_2; FP64: 0                  */
+  double rhs_mean;         /* cell-volume-weighted mean removed from the rhs         */
+  double rhs_absmax;       /* max |rhs|                                              */
+  double max_div;          /* afid_project / substep: max |D u| after projection     */
+  double err_estimate;     /* mixed: estimated relative error of phi (stopping rule:
+                              ||d_k||^2/||d_{k-1}|| <= refine_tol ||phi||, d_k the
+                              k-th correction); FP64: 0                              */
+} afid_info;
+
+typedef struct afid_ctx afid_ctx;
+
+/* Create a context for one grid on the current CUDA device. `stream` is a
+ * cudaStream_t (NULL = legacy default stream). Allocates all workspace
+ * (afid_workspace_bytes) and precomputes the metric, the twiddle tables and
+ * the Thomas factor table of every wavenumber pair. Returns AFID_ERR_OOM if
+ * the device cannot hold the workspace. Sec. 2.2 (workspace reuse: Sec. 3.3). */
+afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void* stream,
+                        afid_ctx** out);
+afid_status afid_destroy(afid_ctx* ctx);
+afid_status afid_set_stream(afid_ctx* ctx, void* stream);
+size_t afid_workspace_bytes(const afid_grid_desc* desc);
+
+/* Poisson solve, Sec. 2.2: phi with L phi = rhs - mean_W(rhs), mean_W(phi) = 0,
+ * where L is the 7-point Laplacian of the staggered grid (periodic x, y; zero
+ * flux at the walls) and mean_W the cell-volume-weighted mean. Forward
+ * real-to-complex FFT in x, complex FFT in y, one Thomas solve per (kx, ky)
+ * with modified wavenumbers 4 sin^2(pi k/N)/h^2, exact integration of the
+ * singular (0,0) mode, inverse FFTs. rhs and phi: device [nz][ny][nx]; they
+ * may alias. In AFID_MIXED the solve is FP32 with FP64 residual refinement. */
+afid_status afid_poisson_solve(afid_ctx* ctx, const double* rhs, double* phi, afid_info* info);
+
+/* Pressure correction, Sec. 2.1 and the last paragraph of Sec. 2.2: with
+ * b = D(u)/s, phi = L^-1 b, then u -= s G_x phi, v -= s G_y phi,
+ * w -= s G_z phi on interior z-faces, p += phi - beta dzz phi. The divergence
+ * is fused into the forward x-transform. u, v, p: [nz][ny][nx]; w:
+ * [nz+1][ny][nx], updated in place. s > 0. info->max_div is measured after the
+ * projection when info is non-NULL. */
+afid_status afid_project(afid_ctx* ctx, double* u, double* v, double* w, double* p, double s,
+                         double beta, afid_info* info);
+
+/* CFL number of Listing 1: max over cells of 0.5(|u_i+u_i+1|/dx +
+ * |v_j+v_j+1|/dy + |w_k+w_k+1|/dzc_k), floored at 1e-8. Writes one double to
+ * the DEVICE pointer cflm_dev, and dt = min(cfl/cflm, dt_max) to the context's
+ * device-resident time step used by afid_rk3_substep when it is given dt <= 0. */
+afid_status afid_cfl(afid_ctx* ctx, const double* u, const double* v, const double* w,
+                     double cfl, double dt_max, double* cflm_dev);
+
+/* One low-storage RK3 / Crank-Nicolson substep l in {0,1,2}, Sec. 2.1:
+ * H = -A(u) + nu (dxx+dyy) q (+ buoyancy T on w), R = dt[gamma_l H + rho_l
+ * Hprev - alpha_l G p + alpha_l nu dzz q], (I - beta_l dzz) dq = R with
+ * beta_l = alpha_l dt nu/2 (kappa for T), q += dq, then the pressure
+ * correction with s = alpha_l dt. gamma = (8/15, 5/12, 3/4), rho = (0, -17/60,
+ * -5/12), alpha = gamma + rho. H* arrays are in/out: on entry the previous
+ * substep's explicit terms (unused when l = 0), on exit this substep's. T and
+ * HT may both be NULL (no scalar). dt <= 0 uses the device-resident dt set by
+ * afid_cfl. */
+afid_status afid_rk3_substep(afid_ctx* ctx, int l, double dt, double* u, double* v, double* w,
+                             double* T, double* p, double* Hu, double* Hv, double* Hw,
+                             double* HT, afid_info* info);
+
+/* max |D u| over all cells (divergence of Sec. 2.2 step 1) into a DEVICE double. */
+afid_status afid_max_divergence(afid_ctx* ctx, const double* u, const double* v, const double* w,
+                                double* out_dev);
+
+/* Transpose of the linear map rhs -> phi of afid_poisson_solve (exact
+ * transpose: grhs = W_c solve(W_c^-1 gphi), W_c the cell volumes). gphi and
+ * grhs: device [nz][ny][nx]; may alias. Always FP64. */
+afid_status afid_poisson_solve_adjoint(afid_ctx* ctx, const double* gphi, double* grhs);
+
+/* Transpose of the linear map (u, v, w, p) -> afid_project(u, v, w, p, s, beta).
+ * On entry gu, gv, gw, gp hold the cotangents of the outputs; on exit the
+ * cotangents of the inputs (in place). Always FP64. */
+afid_status afid_project_adjoint(afid_ctx* ctx, double* gu, double* gv, double* gw, double* gp,
+                                 double s, double beta);
+
+/* Transpose of the Jacobian of afid_rk3_substep at the forward input
+ * (u, v, w, T) (device, unchanged), with the same l and dt (dt must be > 0;
+ * the adjoint treats dt as a constant). On entry g* hold the cotangents of the
+ * substep's outputs (u, v, w, T, p, Hu, Hv, Hw, HT); on exit the cotangents of
+ * its inputs (u, v, w, T, p, Hprev_u, ..., Hprev_T), in place. T/gT/gHT may be
+ * NULL together. */
+afid_status afid_rk3_substep_adjoint(afid_ctx* ctx, int l, double dt, const double* u,
+                                     const double* v, const double* w, const double* T,
+                                     double* gu, double* gv, double* gw, double* gT, double* gp,
+                                     double* gHu, double* gHv, double* gHw, double* gHT);
+
+/* Last status text. */
+const char* afid_status_string(afid_status s);
+
+/* Number of kernels launched by this context since creation (instrumentation). */
+long long afid_kernel_launches(const afid_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFID_H */

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libafid (include/afid.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of libafid.so; this module checks
+tensor shapes, dtypes, devices and contiguity, passes raw device pointers and
+the current CUDA stream, and turns status codes into exceptions. There is no
+fallback: if the library is missing or no GPU is present, calls raise.
+
+Field layout (C order, x fastest, torch.float64, CUDA, contiguous):
+  u, v, p, phi, rhs   [nz][ny][nx]
+  w, T                [nz+1][ny][nx]   (planes 0 and nz are the walls)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libafid.so")
+
+AFID_OK = 0
+AFID_ERR_INVALID_ARG = 1
+AFID_ERR_UNSUPPORTED_SIZE = 2
+AFID_ERR_ALIGNMENT = 3
+AFID_ERR_NOT_CONVERGED = 4
+AFID_ERR_INCONSISTENT_RHS = 5
+AFID_ERR_CUDA = 6
+AFID_ERR_OOM = 7
+AFID_FP64 = 0
+AFID_MIXED = 1
+AFID_POISSON_ONLY = 1
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double),
+                ("ly", C.c_double), ("zf", C.POINTER(C.c_double)), ("precision", C.c_int),
+                ("refine_tol", C.c_double), ("refine_max_iter", C.c_int), ("flags", C.c_int)]
+
+
+class PhysDesc(C.Structure):
+    _fields_ = [("nu", C.c_double), ("kappa", C.c_double), ("buoyancy", C.c_double),
+                ("u_bot", C.c_double), ("u_top", C.c_double), ("T_bot", C.c_double),
+                ("T_top", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rel_residual", C.c_double), ("rhs_mean", C.c_double),
+                ("rhs_absmax", C.c_double), ("max_div", C.c_double), ("err_estimate", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AfidError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, status_string(status), status))
+
+
+_lib = None
+P = C.c_void_p
+D = C.c_double
+I = C.c_int
+
+_SIGS = {
+    "afid_create": (I, [C.POINTER(GridDesc), C.POINTER(PhysDesc), P, C.POINTER(P)]),
+    "afid_destroy": (I, [P]),
+    "afid_set_stream": (I, [P, P]),
+    "afid_workspace_bytes": (C.c_size_t, [C.POINTER(GridDesc)]),
+    "afid_poisson_solve": (I, [P, P, P, C.POINTER(Info)]),
+    "afid_project": (I, [P, P, P, P, P, D, D, C.POINTER(Info)]),
+    "afid_cfl": (I, [P, P, P, P, D, D, P]),
+    "afid_rk3_substep": (I, [P, I, D, P, P, P, P, P, P, P, P, P, C.POINTER(Info)]),
+    "afid_max_divergence": (I, [P, P, P, P, P]),
+    "afid_poisson_solve_adjoint": (I, [P, P, P]),
+    "afid_project_adjoint": (I, [P, P, P, P, P, D, D]),
+    "afid_rk3_substep_adjoint": (I, [P, I, D, P, P, P, P, P, P, P, P, P, P, P, P, P]),
+    "afid_status_string": (C.c_char_p, [I]),
+    "afid_kernel_launches": (C.c_longlong, [P]),
+}
+
+
+def lib():
+    """Load libafid.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libafid.so not found at %s: run paper_1705_01423_gb300/build.py "
+                               "(there is no CPU fallback)" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().afid_status_string(s).decode()
+    except Exception:
+        return "status %d" % s
+
+
+def _ptr(t, shape, name):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return C.c_void_p(t.data_ptr())
+
+
+def _check(st: int, where: str, allow=()):
+    if st != AFID_OK and st not in allow:
+        raise AfidError(st, where)
+    return st
+
+
+@dataclass
+class Physics:
+    nu: float = 0.0
+    kappa: float = 0.0
+    buoyancy: float = 0.0
+    u_bot: float = 0.0
+    u_top: float = 0.0
+    T_bot: float = 0.0
+    T_top: float = 0.0
+
+
+class Context:
+    """One grid on the current CUDA device (afid_create / afid_destroy)."""
+
+    def __init__(self, nx, ny, nz, lx, ly, zf, precision="fp64", refine_tol=1e-12,
+                 refine_max_iter=10, phys: Physics | None = None, poisson_only=False,
+                 stream=None):
+        import torch
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.lx, self.ly = float(lx), float(ly)
+        self._zf = np.ascontiguousarray(np.asarray(zf, dtype=np.float64))
+        if self._zf.shape != (self.nz + 1,):
+            raise ValueError("zf must hold nz+1 face coordinates")
+        self.precision = precision
+        self.phys = phys or Physics()
+        desc = GridDesc(self.nx, self.ny, self.nz, self.lx, self.ly,
+                        self._zf.ctypes.data_as(C.POINTER(C.c_double)),
+                        AFID_MIXED if precision == "mixed" else AFID_FP64, float(refine_tol),
+                        int(refine_max_iter), AFID_POISSON_ONLY if poisson_only else 0)
+        self._desc = desc
+        ph = PhysDesc(self.phys.nu, self.phys.kappa, self.phys.buoyancy, self.phys.u_bot,
+                      self.phys.u_top, self.phys.T_bot, self.phys.T_top)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        h = C.c_void_p()
+        _check(lib().afid_create(C.byref(desc), C.byref(ph), C.c_void_p(stream.cuda_stream),
+                                 C.byref(h)), "afid_create")
+        self._h = h
+        self.workspace_bytes = int(lib().afid_workspace_bytes(C.byref(desc)))
+
+    # shapes
+    @property
+    def cell(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def face(self):
+        return (self.nz + 1, self.ny, self.nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().afid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(lib().afid_set_stream(self._h, C.c_void_p(stream.cuda_stream)), "afid_set_stream")
+
+    def kernel_launches(self) -> int:
+        return int(lib().afid_kernel_launches(self._h))
+
+    # ---- forward calls
+    def poisson_solve(self, rhs, phi=None, info=False):
+        import torch
+        if phi is None:
+            phi = torch.empty_like(rhs)
+        inf = Info() if info else None
+        st = lib().afid_poisson_solve(self._h, _ptr(rhs, self.cell, "rhs"), _ptr(phi, self.cell, "phi"),
+                                      C.byref(inf) if inf else None)
+        _check(st, "afid_poisson_solve", allow=(AFID_ERR_NOT_CONVERGED, AFID_ERR_INCONSISTENT_RHS))
+        if info:
+            d = inf.as_dict()
+            d["status"] = st
+            return phi, d
+        return phi
+
+    def project(self, u, v, w, p, s=1.0, beta=0.0, info=False):
+        inf = Info() if info else None
+        st = lib().afid_project(self._h, _ptr(u, self.cell, "u"), _ptr(v, self.cell, "v"),
+                                _ptr(w, self.face, "w"), _ptr(p, self.cell, "p"), float(s),
+                                float(beta), C.byref(inf) if inf else None)
+        _check(st, "afid_project", allow=(AFID_ERR_NOT_CONVERGED, AFID_ERR_INCONSISTENT_RHS))
+        if info:
+            d = inf.as_dict()
+            d["status"] = st
+            return d
+        return None
+
+    def cfl(self, u, v, w, cfl=0.7, dt_max=1e-2):
+        """Returns the CFL number as a 1-element device tensor and sets the
+        context's device-resident dt = min(cfl/cflm, dt_max)."""
+        import torch
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+        _check(lib().afid_cfl(self._h, _ptr(u, self.cell, "u"), _ptr(v, self.cell, "v"),
+                              _ptr(w, self.face, "w"), float(cfl), float(dt_max),
+                              C.c_void_p(out.data_ptr())), "afid_cfl")
+        return out
+
+    def max_divergence(self, u, v, w):
+        import torch
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+        _check(lib().afid_max_divergence(self._h, _ptr(u, self.cell, "u"), _ptr(v, self.cell, "v"),
+                                         _ptr(w, self.face, "w"), C.c_void_p(out.data_ptr())),
+               "afid_max_divergence")
+        return out
+
+    def rk3_substep(self, l, dt, u, v, w, T, p, Hu, Hv, Hw, HT, info=False):
+        """dt <= 0 uses the dt set by the last cfl() call (device resident)."""
+        inf = Info() if info else None
+        st = lib().afid_rk3_substep(self._h, int(l), float(dt), _ptr(u, self.cell, "u"),
+                                    _ptr(v, self.cell, "v"), _ptr(w, self.face, "w"),
+                                    _ptr(T, self.face, "T"), _ptr(p, self.cell, "p"),
+                                    _ptr(Hu, self.cell, "Hu"), _ptr(Hv, self.cell, "Hv"),
+                                    _ptr(Hw, self.face, "Hw"), _ptr(HT, self.face, "HT"),
+                                    C.byref(inf) if inf else None)
+        _check(st, "afid_rk3_substep", allow=(AFID_ERR_NOT_CONVERGED, AFID_ERR_INCONSISTENT_RHS))
+        if info:
+            d = inf.as_dict()
+            d["status"] = st
+            return d
+        return None
+
+    def rk3_step(self, state, H, dt):
+        """Three substeps in place; state = (u, v, w, T, p), H = (Hu, Hv, Hw, HT)."""
+        u, v, w, T, p = state
+        for l in range(3):
+            self.rk3_substep(l, dt, u, v, w, T, p, *H)
+
+    # ---- adjoints
+    def poisson_solve_adjoint(self, gphi, grhs=None):
+        import torch
+        if grhs is None:
+            grhs = torch.empty_like(gphi)
+        _check(lib().afid_poisson_solve_adjoint(self._h, _ptr(gphi, self.cell, "gphi"),
+                                                _ptr(grhs, self.cell, "grhs")),
+               "afid_poisson_solve_adjoint")
+        return grhs
+
+    def project_adjoint(self, gu, gv, gw, gp, s=1.0, beta=0.0):
+        _check(lib().afid_project_adjoint(self._h, _ptr(gu, self.cell, "gu"), _ptr(gv, self.cell, "gv"),
+                                          _ptr(gw, self.face, "gw"), _ptr(gp, self.cell, "gp"),
+                                          float(s), float(beta)), "afid_project_adjoint")
+
+    def rk3_substep_adjoint(self, l, dt, u, v, w, T, gu, gv, gw, gT, gp, gHu, gHv, gHw, gHT):
+        _check(lib().afid_rk3_substep_adjoint(
+            self._h, int(l), float(dt), _ptr(u, self.cell, "u"), _ptr(v, self.cell, "v"),
+            _ptr(w, self.face, "w"), _ptr(T, self.face, "T"), _ptr(gu, self.cell, "gu"),
+            _ptr(gv, self.cell, "gv"), _ptr(gw, self.face, "gw"), _ptr(gT, self.face, "gT"),
+            _ptr(gp, self.cell, "gp"), _ptr(gHu, self.cell, "gHu"), _ptr(gHv, self.cell, "gHv"),
+            _ptr(gHw, self.face, "gHw"), _ptr(gHT, self.face, "gHT")), "afid_rk3_substep_adjoint")

@@ -1,0 +1,152 @@
+// Internal definitions shared by the libafid translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/afid.h"
+#include "fft.cuh"
+
+namespace afid {
+
+// Wall-normal metric, device resident (one allocation). Index ranges:
+//   dzc, rdzc            [nz]     cell widths and their inverses
+//   dzf, rdzf            [nz+1]   centre spacings; dzf[0] = dzc[0]/2, dzf[nz] = dzc[nz-1]/2
+//   pa, pc               [nz]     Poisson operator (zero-flux walls): pa[0] = pc[nz-1] = 0
+//   ca, cc               [nz]     cell operator with Dirichlet walls half a cell away
+//   fa, fc               [nz+1]   face operator on interior faces k = 1..nz-1
+//   wlo, whi             [nz+1]   volume weights of the cell->face interpolation
+//                                 (dzc[k-1], dzc[k]) / (2 dzf[k]) on interior faces
+struct Metric {
+  const double *dzc, *rdzc, *dzf, *rdzf, *pa, *pc, *ca, *cc, *fa, *fc, *wlo, *whi;
+};
+
+// Small device-resident scalars (one allocation).
+enum Scalar {
+  S_DT = 0,        // time step set by afid_cfl
+  S_CFLM,          // last CFL number
+  S_RHS_MEAN,      // weighted mean removed from the last rhs
+  S_RHS_ABSMAX,    // max |rhs| of the last solve (as an ordered uint64 bit pattern)
+  S_MAXDIV,        // max |div| (bit pattern)
+  S_BNORM2,        // mixed: ||b - mean||_2^2
+  S_RNORM2,        // mixed: ||r||_2^2 of the last residual
+  S_BMEAN,         // mixed: weighted mean of b
+  S_CONVERGED,     // mixed: 1.0 when converged
+  S_ITERS,         // mixed: iterations done
+  S_PROJ_S,        // projection scale s (alpha_l dt in a substep)
+  S_PROJ_BETA,     // pressure-update coefficient beta
+  S_DNORM2,        // mixed: ||delta||_2^2 of the last correction
+  S_DPREV2,        // mixed: ||delta||_2^2 of the correction before it
+  S_PHINORM2,      // mixed: ||phi||_2^2 after the last correction
+  S_ERREST,        // mixed: estimated relative error of phi
+  S_COUNT = 16
+};
+
+struct Grid {
+  int nx, ny, nz;
+  int M;         // nx / 2
+  int P;         // spectral row pitch in complex elements (>= M + 1)
+  int nyh;       // ny / 2 + 1 (rows of the Thomas factor table)
+  double dx, dy, rdx, rdy, rdx2, rdy2;
+};
+
+}  // namespace afid
+
+struct afid_ctx {
+  afid::Grid g;
+  double lx, ly;
+  int prec;
+  double tol;
+  int max_iter;
+  int flags;
+  afid_phys phys;
+  cudaStream_t stream;
+  int device;
+  int num_sms;
+
+  // metric
+  void* metric_buf;
+  afid::Metric m;
+  // twiddle tables exp(-2 pi i m / N): x table of nx entries, y table of ny entries
+  double2 *twx64, *twy64;
+  float2 *twx32, *twy32;
+  // Thomas factor tables mtab[k][kyh][kx] (kyh = min(ky, ny-ky)); mtab64 always,
+  // mtab32 in mixed mode; low-mode mask threshold for mixed mode
+  double* mtab64;
+  float* mtab32;
+  double lam_thr;
+  double* lamx;  // [M+1]
+  double* lamy;  // [nyh]
+  // spectral workspace [nz][ny][P] complex (double2 in FP64, float2 in mixed)
+  void* spec;
+  // physical workspace
+  double* phi;    // [nz][ny][nx]
+  double* res;    // mixed residual [nz][ny][nx]
+  double* bbuf;   // mixed: FP64 right-hand side kept for the residual [nz][ny][nx]
+  double* R[4];   // substep right-hand sides (u, v: cells; w, T: faces)
+  double* cntab;  // Crank-Nicolson factor tables [3][4][nz+1]
+  // mixed precision: FP32 copies of the Poisson off-diagonals, the low-mode list
+  // (ky, kx) solved in FP64 and its FP64 scratch column
+  float *pa32, *pc32;
+  int2* low_modes;
+  int nlow;
+  double2* low_scratch;
+  double* scal;   // device scalars (Scalar enum)
+  double* part;   // reduction partials
+  int part_len;
+  double* part2;  // mixed: per-block (||delta||^2, ||phi||^2) of the accumulate pass
+  int part2_len;
+  size_t bytes;
+  long long launches;
+};
+
+namespace afid {
+
+// launchers (stream-ordered; return cudaError_t of the launch)
+cudaError_t init_thomas_tables(afid_ctx* c);
+// Direct FP64 solve of L phi = src / s, src = rhs (rhs != NULL) or D(u, v, w);
+// s is read from the device scalar S_PROJ_S when `dev_s`, else 1.
+cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, const double* v,
+                           const double* w, bool dev_s, double* phi, bool want_stats);
+int c2r_blocks(const Grid& g);
+// Mixed-precision refined solve of L phi = b (FP64 b, resident) into phi.
+cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi);
+// b = D(u, v, w) / s (s from S_PROJ_S)
+cudaError_t divergence_to(afid_ctx* c, const double* u, const double* v, const double* w, double* b);
+// projection with s, beta read from S_PROJ_S / S_PROJ_BETA
+cudaError_t project(afid_ctx* c, double* u, double* v, double* w, double* p, const double* phi);
+cudaError_t set_proj_scalars(afid_ctx* c, double s, double beta);
+cudaError_t max_divergence(afid_ctx* c, const double* u, const double* v, const double* w,
+                           double* out_dev);
+cudaError_t cfl(afid_ctx* c, const double* u, const double* v, const double* w, double cfl,
+                double dt_max, double* cflm_dev);
+cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const double* v,
+                         const double* w, const double* T, const double* p, double* Hu,
+                         double* Hv, double* Hw, double* HT);
+cudaError_t cn_tables(afid_ctx* c, int l, double dt);
+cudaError_t cn_sweeps(afid_ctx* c, double* u, double* v, double* w, double* T);
+cudaError_t scale_cells(afid_ctx* c, const double* in, double* out, bool forward);
+cudaError_t adjoint_explicit(afid_ctx* c, int l, double dt, const double* u, const double* v,
+                             const double* w, const double* T, double* gu, double* gv,
+                             double* gw, double* gT, double* gp, double* gHu, double* gHv,
+                             double* gHw, double* gHT);
+// R_q = A_q^-T g_q for the four Crank-Nicolson operators (g_q unchanged)
+cudaError_t cn_sweeps_adjoint(afid_ctx* c, double* gu, double* gv, double* gw, double* gT);
+cudaError_t project_adjoint_pre(afid_ctx* c, double* gu, double* gv, double* gw, const double* gp,
+                                double s, double beta);
+cudaError_t project_adjoint_post(afid_ctx* c, double* gu, double* gv, double* gw, double* gp,
+                                 const double* psi, double s, double beta);
+
+// RK3 coefficients (Sec. 2.1, low-storage set): gamma, rho, alpha = gamma + rho
+__host__ __device__ inline double rk_gamma(int l) { return l == 0 ? 8.0 / 15.0 : (l == 1 ? 5.0 / 12.0 : 3.0 / 4.0); }
+__host__ __device__ inline double rk_rho(int l) { return l == 0 ? 0.0 : (l == 1 ? -17.0 / 60.0 : -5.0 / 12.0); }
+__host__ __device__ inline double rk_alpha(int l) { return rk_gamma(l) + rk_rho(l); }
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Ordered bit pattern of a non-negative double for atomicMax.
+__device__ __forceinline__ unsigned long long dbl_key(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+
+}  // namespace afid

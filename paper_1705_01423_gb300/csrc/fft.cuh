@@ -1,0 +1,141 @@
+// Shared-memory Stockham FFT building blocks (radix 8 / 4 / 2) for sm_103a.
+//
+// One line of N = 2^n complex points lives in shared memory with one padding
+// slot every 8 elements (pad(m) = m + m/8), so that the stride-R writes of a
+// Stockham pass spread over the banks. Each thread owns 8 complex values per
+// pass: one radix-8 butterfly, two radix-4 or four radix-2 butterflies. A line
+// is transformed by N/8 threads; the pass sequence is radix 8 while at least
+// three factors of two remain, then one radix-4 or radix-2 pass (the first
+// pass needs no twiddles, so the large radix goes first).
+//
+// Twiddles come from a table tw[m] = exp(-2 pi i m / NT) of the table length
+// NT (a multiple of N), computed on the host in FP64; the transform of length
+// N reads it with index stride NT / N. Forward = exp(-), inverse = exp(+)
+// (conjugated twiddles), both unnormalised.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace afid {
+
+template <typename R> struct cplx;
+template <> struct cplx<double> { using T = double2; };
+template <> struct cplx<float> { using T = float2; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { return C{a.x * s, a.y * s}; }
+
+__host__ __device__ __forceinline__ int pad8(int m) { return m + (m >> 3); }
+
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C rot_mi(C a) {
+  return INV ? C{-a.y, a.x} : C{a.y, -a.x};
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C& a0, C& a1) {
+  C t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = rot_mi<INV>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C* a) {
+  using R = decltype(a[0].x);
+  const R h = (R)0.70710678118654752440;  // 1/sqrt(2)
+  // even / odd halves
+  dft4<INV>(a[0], a[2], a[4], a[6]);
+  dft4<INV>(a[1], a[3], a[5], a[7]);
+  // twiddle the odd half by w8^k, k = 1, 2, 3
+  C o1 = a[3], o2 = a[5], o3 = a[7];
+  if (!INV) {
+    o1 = C{(o1.x + o1.y) * h, (o1.y - o1.x) * h};
+    o3 = C{(o3.y - o3.x) * h, -(o3.x + o3.y) * h};
+  } else {
+    o1 = C{(o1.x - o1.y) * h, (o1.x + o1.y) * h};
+    o3 = C{-(o3.x + o3.y) * h, (o3.x - o3.y) * h};
+  }
+  o2 = rot_mi<INV>(o2);
+  C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6], o0 = a[1];
+  a[0] = cadd(e0, o0);
+  a[4] = csub(e0, o0);
+  a[1] = cadd(e1, o1);
+  a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2);
+  a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3);
+  a[7] = csub(e3, o3);
+}
+
+// One Stockham pass of radix R on a padded shared-memory line `buf` of N points,
+// span p (size of the sub-transforms already done). `t` in [0, N/8) is the
+// thread's index within the line. All reads happen before the barrier, all
+// writes after it, so the pass is in place. The caller guarantees that every
+// thread of the block calls this (barriers inside).
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void stockham_pass(C* buf, int N, int p, const C* tw, int twstride,
+                                              int t, bool active) {
+  constexpr int B = 8 / R;  // butterflies per thread
+  C x[8];
+  const int nb = N / R;
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * (N / 8);
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[b * R + r] = buf[pad8(j + r * nb)];
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * (N / 8);
+      const int k = j & (p - 1);
+      C* y = x + b * R;
+      if (p > 1) {
+        const int step = (N / (p * R)) * twstride;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const C w = tw[r * k * step];
+          y[r] = INV ? cmulc(y[r], w) : cmul(y[r], w);
+        }
+      }
+      if (R == 8) dft8<INV>(y);
+      if (R == 4) dft4<INV>(y[0], y[1], y[2], y[3]);
+      if (R == 2) dft2<INV>(y[0], y[1]);
+      const int o = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[pad8(o + r * p)] = y[r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full N-point transform of one padded line; N = 2^n, 8 <= N.
+template <bool INV, typename C>
+__device__ __forceinline__ void fft_line(C* buf, int N, const C* tw, int twstride, int t, bool active) {
+  int p = 1;
+  while (N / p >= 8) {
+    stockham_pass<8, INV>(buf, N, p, tw, twstride, t, active);
+    p *= 8;
+  }
+  if (N / p == 4) stockham_pass<4, INV>(buf, N, p, tw, twstride, t, active);
+  else if (N / p == 2) stockham_pass<2, INV>(buf, N, p, tw, twstride, t, active);
+}
+
+}  // namespace afid

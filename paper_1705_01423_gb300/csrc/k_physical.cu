@@ -1,0 +1,552 @@
+// Physical-space stages: projection and pressure update (Sec. 2.2 last
+// paragraph), divergence check, CFL (Listing 1), the explicit terms of the
+// RK3 substep with the right-hand side of its Crank-Nicolson systems (Sec.
+// 2.1), the wall-normal Crank-Nicolson sweeps, and the FP64 residual and
+// norms of the mixed-precision refinement.
+//
+// Stencil kernels run one thread per grid point with x along threadIdx.x, so
+// every neighbour load of a warp is a contiguous 256-byte row segment (the
+// x +- 1 neighbours hit L1). The wall-normal sweeps run one thread per (x, y)
+// column and walk z, again coalesced across x.
+#include "afid_internal.cuh"
+
+namespace afid {
+
+__device__ __forceinline__ size_t at(const Grid& g, int k, int j, int i) {
+  return ((size_t)k * g.ny + j) * g.nx + i;
+}
+
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum, result valid in thread 0 (blockDim.x multiple of 32, <= 1024)
+__device__ double block_sum(double v) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+static inline dim3 point_grid(const Grid& g, int nzp, int& bx) {
+  bx = g.nx < 128 ? g.nx : 128;
+  return dim3(g.nx / bx, g.ny, nzp);
+}
+
+// ---------------------------------------------------------------------------
+// Projection and pressure update:
+//   u -= s (phi_i - phi_{i-1})/dx, v -= s (phi_j - phi_{j-1})/dy,
+//   w_k -= s (phi_k - phi_{k-1})/dzf_k (interior faces),
+//   p += phi - beta [pc_k (phi_{k+1} - phi_k) - pa_k (phi_k - phi_{k-1})].
+__global__ void k_project(Grid g, Metric m, double* __restrict__ u, double* __restrict__ v,
+                          double* __restrict__ w, double* __restrict__ p,
+                          const double* __restrict__ phi, const double* __restrict__ scal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  const double s = scal[S_PROJ_S], beta = scal[S_PROJ_BETA];
+  const int im = (i - 1) & (g.nx - 1), jm = (j - 1) & (g.ny - 1);
+  const size_t c = at(g, k, j, i);
+  const double f = phi[c];
+  const double fkm = k > 0 ? phi[c - (size_t)g.nx * g.ny] : f;
+  const double fkp = k < g.nz - 1 ? phi[c + (size_t)g.nx * g.ny] : f;
+  u[c] -= s * (f - phi[at(g, k, j, im)]) * g.rdx;
+  v[c] -= s * (f - phi[at(g, k, jm, i)]) * g.rdy;
+  if (k > 0) w[c] -= s * (f - fkm) * m.rdzf[k];
+  if (p) p[c] += f - beta * (m.pc[k] * (fkp - f) - m.pa[k] * (f - fkm));
+}
+
+cudaError_t project(afid_ctx* c, double* u, double* v, double* w, double* p, const double* phi) {
+  int bx;
+  dim3 grd = point_grid(c->g, c->g.nz, bx);
+  k_project<<<grd, bx, 0, c->stream>>>(c->g, c->m, u, v, w, p, phi, c->scal);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+__global__ void k_set_proj(double* scal, double s, double beta) {
+  scal[S_PROJ_S] = s;
+  scal[S_PROJ_BETA] = beta;
+}
+
+cudaError_t set_proj_scalars(afid_ctx* c, double s, double beta) {
+  k_set_proj<<<1, 1, 0, c->stream>>>(c->scal, s, beta);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// b = D(u, v, w) / s (the divergence of Sec. 2.2 step 1), s = S_PROJ_S
+__global__ void k_div(Grid g, Metric m, const double* __restrict__ u, const double* __restrict__ v,
+                      const double* __restrict__ w, double* __restrict__ b,
+                      const double* __restrict__ scal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  const double rs = 1.0 / scal[S_PROJ_S];
+  const size_t c = at(g, k, j, i);
+  const int ip = (i + 1) & (g.nx - 1), jp = (j + 1) & (g.ny - 1);
+  const double d = (u[at(g, k, j, ip)] - u[c]) * g.rdx + (v[at(g, k, jp, i)] - v[c]) * g.rdy +
+                   (w[c + (size_t)g.nx * g.ny] - w[c]) * m.rdzc[k];
+  b[c] = d * rs;
+}
+
+cudaError_t divergence_to(afid_ctx* c, const double* u, const double* v, const double* w, double* b) {
+  int bx;
+  dim3 grd = point_grid(c->g, c->g.nz, bx);
+  k_div<<<grd, bx, 0, c->stream>>>(c->g, c->m, u, v, w, b, c->scal);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// max |D u| over cells (grid-stride, one atomic per warp)
+__global__ void k_maxdiv(Grid g, Metric m, const double* __restrict__ u,
+                         const double* __restrict__ v, const double* __restrict__ w,
+                         unsigned long long* out) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  double mx = 0.0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.nx);
+    const size_t r = c / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    const int ip = (i + 1) & (g.nx - 1), jp = (j + 1) & (g.ny - 1);
+    const double d = (u[at(g, k, j, ip)] - u[c]) * g.rdx + (v[at(g, k, jp, i)] - v[c]) * g.rdy +
+                     (w[c + (size_t)g.nx * g.ny] - w[c]) * m.rdzc[k];
+    mx = fmax(mx, fabs(d));
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, dbl_key(mx));
+}
+
+cudaError_t max_divergence(afid_ctx* c, const double* u, const double* v, const double* w,
+                           double* out_dev) {
+  cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double), c->stream);
+  if (e) return e;
+  k_maxdiv<<<c->num_sms * 8, 256, 0, c->stream>>>(c->g, c->m, u, v, w,
+                                                  reinterpret_cast<unsigned long long*>(out_dev));
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CFL of Listing 1: 0.5 max(|u_i+u_i+1|/dx + |v_j+v_j+1|/dy + |w_k+w_k+1|/dzc_k),
+// floored at 1e-8; dt = min(cfl/cflm, dt_max).
+__global__ void k_cfl(Grid g, Metric m, const double* __restrict__ u, const double* __restrict__ v,
+                      const double* __restrict__ w, unsigned long long* out) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  double mx = 0.0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.nx);
+    const size_t r = c / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    const int ip = (i + 1) & (g.nx - 1), jp = (j + 1) & (g.ny - 1);
+    const double q = fabs(u[c] + u[at(g, k, j, ip)]) * g.rdx + fabs(v[c] + v[at(g, k, jp, i)]) * g.rdy +
+                     fabs(w[c] + w[c + (size_t)g.nx * g.ny]) * m.rdzc[k];
+    mx = fmax(mx, q);
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, dbl_key(mx));
+}
+
+__global__ void k_cfl_final(double* scal, double cfl, double dt_max, double* cflm_dev) {
+  const double q = __longlong_as_double((long long)reinterpret_cast<unsigned long long*>(scal)[S_CFLM]);
+  const double cflm = fmax(1e-8, 0.5 * q);
+  if (cflm_dev) *cflm_dev = cflm;
+  scal[S_CFLM] = cflm;
+  scal[S_DT] = fmin(cfl / cflm, dt_max);
+}
+
+cudaError_t cfl(afid_ctx* c, const double* u, const double* v, const double* w, double cflv,
+                double dt_max, double* cflm_dev) {
+  cudaError_t e = cudaMemsetAsync(c->scal + S_CFLM, 0, sizeof(double), c->stream);
+  if (e) return e;
+  k_cfl<<<c->num_sms * 8, 256, 0, c->stream>>>(c->g, c->m, u, v, w,
+                                               reinterpret_cast<unsigned long long*>(c->scal + S_CFLM));
+  k_cfl_final<<<1, 1, 0, c->stream>>>(c->scal, cflv, dt_max, cflm_dev);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Explicit terms H and Crank-Nicolson right-hand sides R of substep l.
+// Thread (i, j, k), k = 0..nz-1, handles u and v at cell k and w and T on
+// face k (k >= 1). Advection is the conservative form with arithmetic face
+// averages; u and v are carried onto z-faces with the volume weights
+// (dzc_{k-1}, dzc_k)/(2 dzf_k).
+struct PhysK {
+  double nu, kappa, buoy, ubot, utop;
+};
+
+__global__ void __launch_bounds__(128) k_rhs(Grid g, Metric m, PhysK ph, int l, double dt_in,
+                                             const double* __restrict__ dt_dev,
+                                             const double* __restrict__ u, const double* __restrict__ v,
+                                             const double* __restrict__ w, const double* __restrict__ T,
+                                             const double* __restrict__ p, double* __restrict__ Hu,
+                                             double* __restrict__ Hv, double* __restrict__ Hw,
+                                             double* __restrict__ HT, double* __restrict__ Ru,
+                                             double* __restrict__ Rv, double* __restrict__ Rw,
+                                             double* __restrict__ RT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int ip = (i + 1) & (nx - 1), im = (i - 1) & (nx - 1);
+  const int jp = (j + 1) & (ny - 1), jm = (j - 1) & (ny - 1);
+  const size_t NXY = (size_t)nx * ny;
+  const double dt = dt_in > 0.0 ? dt_in : *dt_dev;
+  const double gam = rk_gamma(l), rho = rk_rho(l), alp = rk_alpha(l);
+  const size_t c = at(g, k, j, i);
+  const size_t cim = at(g, k, j, im), cip = at(g, k, j, ip);
+  const size_t cjm = at(g, k, jm, i), cjp = at(g, k, jp, i);
+
+  // ---------------- u at (x-face i, cell j, cell k)
+  const double u0 = u[c], uip = u[cip], uim = u[cim], ujp = u[cjp], ujm = u[cjm];
+  const double v0 = v[c], vim = v[cim], vip = v[cip], vjp = v[cjp], vjm = v[cjm];
+  const double vjpim = v[at(g, k, jp, im)];
+  const double ujmip = u[at(g, k, jm, ip)];
+  const double ukm = k > 0 ? u[c - NXY] : ph.ubot;
+  const double ukp = k < nz - 1 ? u[c + NXY] : ph.utop;
+  const double vkm = k > 0 ? v[c - NXY] : 0.0;
+  const double vkp = k < nz - 1 ? v[c + NXY] : 0.0;
+  const double wk = w[c], wkim = w[cim], wkjm = w[cjm];
+  const double wk1 = w[c + NXY], wk1im = w[cim + NXY], wk1jm = w[cjm + NXY];
+  const double rdzc = m.rdzc[k];
+  {
+    const double ur = 0.5 * (u0 + uip), ul = 0.5 * (uim + u0);
+    const double ax = (ur * ur - ul * ul) * g.rdx;
+    const double cj = 0.25 * (vim + v0) * (ujm + u0);
+    const double cjp1 = 0.25 * (vjpim + vjp) * (u0 + ujp);
+    const double ay = (cjp1 - cj) * g.rdy;
+    const double fzk = k > 0 ? 0.25 * (wkim + wk) * (ukm + u0) : 0.0;
+    const double fzk1 = k < nz - 1 ? 0.25 * (wk1im + wk1) * (u0 + ukp) : 0.0;
+    const double az = (fzk1 - fzk) * rdzc;
+    const double lap = (uip - 2.0 * u0 + uim) * g.rdx2 + (ujp - 2.0 * u0 + ujm) * g.rdy2;
+    const double H = -(ax + ay + az) + ph.nu * lap;
+    const double dzz = m.cc[k] * (ukp - u0) - m.ca[k] * (u0 - ukm);
+    const double gp = (p[c] - p[cim]) * g.rdx;
+    double r = gam * H + alp * (ph.nu * dzz - gp);
+    if (l > 0) r += rho * Hu[c];
+    Hu[c] = H;
+    Ru[c] = dt * r;
+  }
+  // ---------------- v at (cell i, y-face j, cell k)
+  {
+    const double cj = 0.25 * (ujm + u0) * (vim + v0);          // corner (x-face i, y-face j)
+    const double cip1 = 0.25 * (ujmip + uip) * (v0 + vip);     // corner (x-face i+1, y-face j)
+    const double ax = (cip1 - cj) * g.rdx;
+    const double vt = 0.5 * (v0 + vjp), vb = 0.5 * (vjm + v0);
+    const double ay = (vt * vt - vb * vb) * g.rdy;
+    const double fzk = k > 0 ? 0.25 * (wkjm + wk) * (vkm + v0) : 0.0;
+    const double fzk1 = k < nz - 1 ? 0.25 * (wk1jm + wk1) * (v0 + vkp) : 0.0;
+    const double az = (fzk1 - fzk) * rdzc;
+    const double lap = (vip - 2.0 * v0 + vim) * g.rdx2 + (vjp - 2.0 * v0 + vjm) * g.rdy2;
+    const double H = -(ax + ay + az) + ph.nu * lap;
+    const double dzz = m.cc[k] * (vkp - v0) - m.ca[k] * (v0 - vkm);
+    const double gp = (p[c] - p[cjm]) * g.rdy;
+    double r = gam * H + alp * (ph.nu * dzz - gp);
+    if (l > 0) r += rho * Hv[c];
+    Hv[c] = H;
+    Rv[c] = dt * r;
+  }
+  if (k == 0) {  // wall planes of the face arrays: no explicit term, no unknown
+    Hw[c] = 0.0;
+    Hw[c + (size_t)nz * NXY] = 0.0;
+    if (T) {
+      HT[c] = 0.0;
+      HT[c + (size_t)nz * NXY] = 0.0;
+    }
+    return;
+  }
+  // ---------------- w and T on interior z-face k
+  const double wlo = m.wlo[k], whi = m.whi[k], rdzf = m.rdzf[k];
+  const double ufi = wlo * ukm + whi * u0;
+  const double ufip = wlo * u[cip - NXY] + whi * uip;
+  const double vfj = wlo * vkm + whi * v0;
+  const double vfjp = wlo * v[cjp - NXY] + whi * vjp;
+  const double wip = w[cip], wjp = w[cjp], wkm = w[c - NXY];
+  const double wc_k = 0.5 * (wk + wk1), wc_km = 0.5 * (wkm + wk);
+  {
+    const double ax = (ufip * 0.5 * (wk + wip) - ufi * 0.5 * (wkim + wk)) * g.rdx;
+    const double ay = (vfjp * 0.5 * (wk + wjp) - vfj * 0.5 * (wkjm + wk)) * g.rdy;
+    const double az = (wc_k * wc_k - wc_km * wc_km) * rdzf;
+    const double lap = (wip - 2.0 * wk + wkim) * g.rdx2 + (wjp - 2.0 * wk + wkjm) * g.rdy2;
+    double H = -(ax + ay + az) + ph.nu * lap;
+    if (T) H += ph.buoy * T[c];
+    const double dzz = m.fc[k] * (wk1 - wk) - m.fa[k] * (wk - wkm);
+    const double gp = (p[c] - p[c - NXY]) * rdzf;
+    double r = gam * H + alp * (ph.nu * dzz - gp);
+    if (l > 0) r += rho * Hw[c];
+    Hw[c] = H;
+    Rw[c] = dt * r;
+  }
+  if (T) {
+    const double t0 = T[c], tim = T[cim], tip = T[cip], tjm = T[cjm], tjp = T[cjp];
+    const double tkm = T[c - NXY], tkp = T[c + NXY];
+    const double ax = (ufip * 0.5 * (t0 + tip) - ufi * 0.5 * (tim + t0)) * g.rdx;
+    const double ay = (vfjp * 0.5 * (t0 + tjp) - vfj * 0.5 * (tjm + t0)) * g.rdy;
+    const double az = (wc_k * 0.5 * (t0 + tkp) - wc_km * 0.5 * (tkm + t0)) * rdzf;
+    const double lap = (tip - 2.0 * t0 + tim) * g.rdx2 + (tjp - 2.0 * t0 + tjm) * g.rdy2;
+    const double H = -(ax + ay + az) + ph.kappa * lap;
+    const double dzz = m.fc[k] * (tkp - t0) - m.fa[k] * (t0 - tkm);
+    double r = gam * H + alp * ph.kappa * dzz;
+    if (l > 0) r += rho * HT[c];
+    HT[c] = H;
+    RT[c] = dt * r;
+  }
+}
+
+cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const double* v,
+                         const double* w, const double* T, const double* p, double* Hu,
+                         double* Hv, double* Hw, double* HT) {
+  int bx;
+  dim3 grd = point_grid(c->g, c->g.nz, bx);
+  PhysK ph{c->phys.nu, c->phys.kappa, c->phys.buoyancy, c->phys.u_bot, c->phys.u_top};
+  k_rhs<<<grd, bx, 0, c->stream>>>(c->g, c->m, ph, l, dt, c->scal + S_DT, u, v, w, T, p, Hu, Hv,
+                                   Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3]);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Crank-Nicolson factor tables for substep l: operator o = 0 (cells, nu),
+// 1 (faces, nu), 2 (faces, kappa); (I - beta dzz) with beta = alpha_l dt d/2.
+// Row k: sub = -beta a_k, diag = 1 + beta (a_k + c_k), sup = -beta c_k;
+// tab[o][0][k] = sub_k, tab[o][1][k] = m_k = 1/(diag_k - sub_k c'_{k-1}),
+// tab[o][2][k] = c'_k = sup_k m_k, tab[o][3][k] = sup_k. Thread 0 also
+// publishes dt, the projection scale s = alpha_l dt and beta = alpha_l dt nu/2.
+__global__ void k_cn_tables(Grid g, Metric m, int l, double dt_in, double* __restrict__ scal,
+                            double nu, double kappa, double* __restrict__ tab) {
+  const int o = threadIdx.x;
+  const double dt = dt_in > 0.0 ? dt_in : scal[S_DT];
+  if (o == 0) {
+    scal[S_DT] = dt;
+    scal[S_PROJ_S] = rk_alpha(l) * dt;
+    scal[S_PROJ_BETA] = rk_alpha(l) * dt * nu * 0.5;
+  }
+  if (o >= 3) return;
+  const double beta = rk_alpha(l) * dt * (o == 2 ? kappa : nu) * 0.5;
+  const int L = g.nz + 1;
+  double* sub = tab + (size_t)o * 4 * L;
+  double* mm = sub + L;
+  double* cp = mm + L;
+  double* sp = cp + L;
+  const int k0 = o == 0 ? 0 : 1, k1 = g.nz;  // rows k0..nz-1
+  double cprev = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    const double a = o == 0 ? m.ca[k] : m.fa[k];
+    const double cc = o == 0 ? m.cc[k] : m.fc[k];
+    const double s = -beta * a, up = -beta * cc, d = 1.0 + beta * (a + cc);
+    const double mk = 1.0 / (d - (k == k0 ? 0.0 : s * cprev));
+    cprev = up * mk;
+    sub[k] = s;
+    mm[k] = mk;
+    cp[k] = cprev;
+    sp[k] = up;
+  }
+}
+
+cudaError_t cn_tables(afid_ctx* c, int l, double dt) {
+  k_cn_tables<<<1, 32, 0, c->stream>>>(c->g, c->m, l, dt, c->scal, c->phys.nu, c->phys.kappa,
+                                       c->cntab);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// One thread per (x, y) column of variable blockIdx.y (0 u, 1 v, 2 w, 3 T);
+// cells k = 0..nz-1 for u, v, interior faces k = 1..nz-1 for w, T.
+// Forward (ADJ = false): elimination writes d' over R, back substitution adds
+// dq = A^-1 R to q. Transposed (ADJ = true): R = A^-T q with A = L U from the
+// same factors (U: diagonal 1/m_k, superdiagonal sup_k; L: unit, subdiagonal
+// sub_k m_{k-1}), solving U^T z = q forward and L^T y = z backward; q is kept.
+template <bool ADJ>
+__global__ void k_cn_sweep(Grid g, const double* __restrict__ tab, double* R0, double* R1,
+                           double* R2, double* R3, double* q0, double* q1, double* q2, double* q3) {
+  const int var = blockIdx.y;
+  double* R = var == 0 ? R0 : var == 1 ? R1 : var == 2 ? R2 : R3;
+  double* q = var == 0 ? q0 : var == 1 ? q1 : var == 2 ? q2 : q3;
+  if (!q) return;
+  const size_t NXY = (size_t)g.nx * g.ny;
+  const size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (col >= NXY) return;
+  const int o = var < 2 ? 0 : (var == 2 ? 1 : 2);
+  const int L = g.nz + 1;
+  const double* sub = tab + (size_t)o * 4 * L;
+  const double* mm = sub + L;
+  const double* cp = mm + L;
+  const double* sp = cp + L;
+  const int k0 = var < 2 ? 0 : 1, k1 = g.nz - 1;  // inclusive range
+  if (!ADJ) {
+    double dp = R[k0 * NXY + col] * mm[k0];
+    R[k0 * NXY + col] = dp;
+    for (int k = k0 + 1; k <= k1; ++k) {
+      dp = (R[k * NXY + col] - sub[k] * dp) * mm[k];
+      R[k * NXY + col] = dp;
+    }
+    double x = dp;
+    q[k1 * NXY + col] += x;
+    for (int k = k1 - 1; k >= k0; --k) {
+      x = R[k * NXY + col] - cp[k] * x;
+      q[k * NXY + col] += x;
+    }
+  } else {
+    double z = q[k0 * NXY + col] * mm[k0];
+    R[k0 * NXY + col] = z;
+    for (int k = k0 + 1; k <= k1; ++k) {
+      z = (q[k * NXY + col] - sp[k - 1] * z) * mm[k];
+      R[k * NXY + col] = z;
+    }
+    double y = z;
+    for (int k = k1 - 1; k >= k0; --k) {
+      y = R[k * NXY + col] - sub[k + 1] * mm[k] * y;
+      R[k * NXY + col] = y;
+    }
+  }
+}
+
+cudaError_t cn_sweeps(afid_ctx* c, double* u, double* v, double* w, double* T) {
+  const size_t NXY = (size_t)c->g.nx * c->g.ny;
+  dim3 grd(ceil_div((long long)NXY, 128), 4);
+  k_cn_sweep<false><<<grd, 128, 0, c->stream>>>(c->g, c->cntab, c->R[0], c->R[1], c->R[2], c->R[3],
+                                                u, v, w, T);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t cn_sweeps_adjoint(afid_ctx* c, double* gu, double* gv, double* gw, double* gT) {
+  const size_t NXY = (size_t)c->g.nx * c->g.ny;
+  dim3 grd(ceil_div((long long)NXY, 128), 4);
+  k_cn_sweep<true><<<grd, 128, 0, c->stream>>>(c->g, c->cntab, c->R[0], c->R[1], c->R[2], c->R[3],
+                                               gu, gv, gw, gT);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision refinement: weighted mean of b, FP64 residual
+// r = (b - mean) - L phi with per-block partial sums of r^2, and the
+// convergence test. All kernels return at once when converged.
+__global__ void k_wmean_partial(Grid g, Metric m, const double* __restrict__ b, double* part) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz, NXY = (size_t)g.nx * g.ny;
+  double s = 0.0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x)
+    s += m.dzc[c / NXY] * b[c];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_wmean_final(Grid g, Metric m, const double* part, int np, double* scal) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    double sw = 0.0;
+    for (int k = 0; k < g.nz; ++k) sw += m.dzc[k];
+    scal[S_BMEAN] = s / (sw * (double)g.nx * (double)g.ny);
+    scal[S_CONVERGED] = 0.0;
+    scal[S_ITERS] = 0.0;
+  }
+}
+
+__global__ void k_residual(Grid g, Metric m, const double* __restrict__ b,
+                           const double* __restrict__ phi, double* __restrict__ r, double* part,
+                           const double* scal) {
+  if (scal[S_CONVERGED] != 0.0) return;
+  const size_t n = (size_t)g.nx * g.ny * g.nz, NXY = (size_t)g.nx * g.ny;
+  const double mean = scal[S_BMEAN];
+  double s = 0.0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.nx);
+    const size_t rr = c / g.nx;
+    const int j = (int)(rr % g.ny), k = (int)(rr / g.ny);
+    const double f = phi[c];
+    const double fkm = k > 0 ? phi[c - NXY] : f;
+    const double fkp = k < g.nz - 1 ? phi[c + NXY] : f;
+    const double L = (phi[at(g, k, j, (i + 1) & (g.nx - 1))] - 2.0 * f + phi[at(g, k, j, (i - 1) & (g.nx - 1))]) * g.rdx2 +
+                     (phi[at(g, k, (j + 1) & (g.ny - 1), i)] - 2.0 * f + phi[at(g, k, (j - 1) & (g.ny - 1), i)]) * g.rdy2 +
+                     m.pc[k] * (fkp - f) - m.pa[k] * (f - fkm);
+    const double rv = (b[c] - mean) - L;
+    r[c] = rv;
+    s += rv * rv;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Convergence test of the refinement. The residual norm is recorded for the
+// report; the stopping rule uses the corrections: with linear convergence the
+// error left after correction k is about ||d_k|| (||d_k|| / ||d_{k-1}||), and
+// the iteration stops once that estimate is below tol ||phi||. (A residual
+// test alone under-estimates the error by up to the condition number of L.)
+__global__ void k_refine_check(const double* part, int np, const double* part2, int np2,
+                               double* scal, double tol, int first) {
+  if (scal[S_CONVERGED] != 0.0) return;
+  double s = 0.0, d2 = 0.0, f2 = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  if (!first)
+    for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+      d2 += part2[2 * i];
+      f2 += part2[2 * i + 1];
+    }
+  s = block_sum(s);
+  d2 = block_sum(d2);
+  f2 = block_sum(f2);
+  if (threadIdx.x == 0) {
+    scal[S_RNORM2] = s;
+    if (first) {
+      scal[S_BNORM2] = s;
+      if (s == 0.0) scal[S_CONVERGED] = 1.0;
+      return;
+    }
+    scal[S_ITERS] += 1.0;
+    const double prev = scal[S_ITERS] > 1.0 ? scal[S_DNORM2] : d2;
+    scal[S_DPREV2] = prev;
+    scal[S_DNORM2] = d2;
+    scal[S_PHINORM2] = f2;
+    const double est2 = prev > 0.0 ? d2 * d2 / prev : 0.0;  // (||d_k||^2 / ||d_{k-1}||)^2
+    scal[S_ERREST] = f2 > 0.0 ? sqrt(est2 / f2) : 0.0;
+    if (s == 0.0 || est2 <= tol * tol * f2) scal[S_CONVERGED] = 1.0;
+  }
+}
+
+cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, const double* skip);
+
+// Mixed-precision refined solve (device-side convergence test, no host sync):
+//   mean = mean_W(b); phi = 0; r = b - mean; ||b - mean||^2
+//   repeat refine_max_iter times (every kernel returns at once once converged):
+//     phi += FP32-spectral-solve(r); r = b - mean - L phi (FP64); converged when
+//     the estimated error ||d_k||^2 / ||d_{k-1}|| <= tol ||phi|| (k_refine_check).
+cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi) {
+  const Grid& g = c->g;
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  const int nb = c->part_len;
+  cudaError_t e;
+  k_wmean_partial<<<nb, 256, 0, c->stream>>>(g, c->m, b, c->part);
+  k_wmean_final<<<1, 1024, 0, c->stream>>>(g, c->m, c->part, nb, c->scal);
+  c->launches += 2;
+  if ((e = cudaMemsetAsync(phi, 0, n * sizeof(double), c->stream))) return e;
+  k_residual<<<nb, 256, 0, c->stream>>>(g, c->m, b, phi, c->res, c->part, c->scal);
+  k_refine_check<<<1, 1024, 0, c->stream>>>(c->part, nb, c->part2, c->part2_len, c->scal, c->tol, 1);
+  c->launches += 2;
+  if ((e = cudaGetLastError())) return e;
+  for (int it = 0; it < c->max_iter; ++it) {
+    if ((e = spectral_solve_fp32(c, c->res, phi, c->scal + S_CONVERGED))) return e;
+    k_residual<<<nb, 256, 0, c->stream>>>(g, c->m, b, phi, c->res, c->part, c->scal);
+    k_refine_check<<<1, 1024, 0, c->stream>>>(c->part, nb, c->part2, c->part2_len, c->scal, c->tol, 0);
+    c->launches += 2;
+    if ((e = cudaGetLastError())) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace afid

@@ -1,0 +1,90 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/afid.h declares; host-side validation rejects bad arguments before
+anything is launched (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1705_01423_gb300 import build
+    build.build()
+    from paper_1705_01423_gb300 import afid
+    return afid.lib()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "afid.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(afid_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+    from paper_1705_01423_gb300 import afid
+    assert sorted(afid.exported_symbols()) == names
+
+
+def test_status_strings(L):
+    for s in range(8):
+        assert L.afid_status_string(s)
+    assert b"unknown" in L.afid_status_string(99)
+
+
+def desc(nx=32, ny=16, nz=8, zf=None, prec=0):
+    from paper_1705_01423_gb300 import afid
+    import synth
+    z = np.ascontiguousarray(synth.tanh_faces(nz, 1.5) if zf is None else zf)
+    d = afid.GridDesc(nx, ny, nz, 1.0, 1.0, z.ctypes.data_as(C.POINTER(C.c_double)), prec, 1e-12, 4, 0)
+    return d, z
+
+
+@pytest.mark.parametrize("nx,ny,nz,code", [(24, 16, 8, 2), (32, 12, 8, 2), (8, 16, 8, 2), (32, 16, 2, 2),
+                                            (8192, 16, 8, 2), (32, 4, 8, 2)])
+def test_create_rejects_unsupported_sizes(L, nx, ny, nz, code):
+    from paper_1705_01423_gb300 import afid
+    d, z = desc(nx, ny, nz, zf=np.linspace(0, 1, nz + 1))
+    h = C.c_void_p()
+    assert L.afid_create(C.byref(d), None, None, C.byref(h)) == code
+    assert not h.value
+    assert L.afid_workspace_bytes(C.byref(d)) == 0
+
+
+def test_create_rejects_bad_faces_and_precision(L):
+    from paper_1705_01423_gb300 import afid
+    z = np.linspace(0, 1, 9)
+    z[4] = z[3]                         # not strictly increasing
+    d, _ = desc(zf=z)
+    h = C.c_void_p()
+    assert L.afid_create(C.byref(d), None, None, C.byref(h)) == afid.AFID_ERR_INVALID_ARG
+    d, z2 = desc(prec=7)
+    assert L.afid_create(C.byref(d), None, None, C.byref(h)) == afid.AFID_ERR_INVALID_ARG
+    assert L.afid_create(None, None, None, C.byref(h)) == afid.AFID_ERR_INVALID_ARG
+    d, z3 = desc()
+    assert L.afid_create(C.byref(d), None, None, None) == afid.AFID_ERR_INVALID_ARG
+
+
+def test_null_context_is_rejected(L):
+    from paper_1705_01423_gb300 import afid
+    assert L.afid_poisson_solve(None, None, None, None) == afid.AFID_ERR_INVALID_ARG
+    assert L.afid_project(None, None, None, None, None, 1.0, 0.0, None) == afid.AFID_ERR_INVALID_ARG
+    assert L.afid_destroy(None) == afid.AFID_ERR_INVALID_ARG
+    assert L.afid_kernel_launches(None) == -1
+
+
+def test_workspace_bytes(L):
+    d, z = desc(64, 32, 16)
+    b64 = L.afid_workspace_bytes(C.byref(d))
+    n = 64 * 32 * 16
+    assert b64 > 8 * n * 5
+    d2, z2 = desc(64, 32, 16, prec=1)
+    assert L.afid_workspace_bytes(C.byref(d2)) > 0
