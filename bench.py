@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 pressure-correction path.
+
+One step = one full FP64 RK3 / Crank-Nicolson time step of the Rayleigh-Benard
+workload (Ra = 1e8, Pr = 1, 512 x 512 x 384 cells, tanh-stretched wall-normal
+grid): the CFL reduction (Listing 1) and three substeps, each with the
+explicit terms, four Crank-Nicolson wall-normal sweeps and the pressure
+correction (divergence fused into the forward x FFT, y FFT, Thomas sweeps,
+inverse FFTs, projection). Inputs are seeded synthetic fields resident in HBM
+(each field is 805 MB, larger than L2, so no flush is needed between steps).
+
+Printed: one JSON line (rank 0) with the headline grid-points/s, the roofline
+of the dominant kernel family (CUDA events around every launch group inside
+the timed region), the FP64 oracle timed on the host cores on a bounded
+sample, the end-to-end number with host buffers, clocks sampled during the
+timed region, and side measurements (Poisson solve alone, FP64 vs mixed).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64: 2 FMA per clock per SM on this part (measured 1.19 TFLOP/s at 1995 MHz
+# with an FMA-chain probe), 152 SMs, 2070 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rb512")
+    ap.add_argument("--no-extra", action="store_true", help="skip the side measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if sm:
+            top = max(sm)
+            loaded = [s for s in sm if s >= 0.5 * top] or sm
+            out = {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ------------------------------------------------------------------ work model
+def family_work(fam: str, w, fp: str = "f64"):
+    """Algorithmic work of one launch group of a kernel family on grid w:
+    (bytes, flops). Bytes are the compulsory HBM traffic of the kernel's own
+    inputs and outputs; flops the standard counts (5 N log2 N per complex
+    N-point FFT, 2.5 N log2 N per real one; stencils counted in FP64
+    operations of their definition, FMA = 2)."""
+    nx, ny, nz = w.nx, w.ny, w.nz
+    n = nx * ny * nz
+    M1 = nx // 2 + 1
+    cs = 16 if fp == "f64" else 8       # complex element
+    rs = 8 if fp == "f64" else 4        # real element in the spectral stages
+    if fam == "r2c_x":      # divergence fused: read u, v, w (8 B each) + write spectrum
+        return 24 * n + cs * M1 * ny * nz, 2.5 * nx * math.log2(nx) * ny * nz + 8 * n
+    if fam == "c2r_x":
+        return cs * M1 * ny * nz + 8 * n, 2.5 * nx * math.log2(nx) * ny * nz
+    if fam == "fft_y":
+        return 2 * cs * M1 * ny * nz, 5 * ny * math.log2(ny) * M1 * nz
+    if fam == "thomas":     # data in/out + reciprocal-pivot table, read once
+        return 2 * cs * M1 * ny * nz + rs * M1 * (ny // 2 + 1) * nz, 14 * M1 * ny * nz
+    if fam == "project":    # read phi, u, v, w, p; write u, v, w, p
+        return 72 * n, 20 * n
+    if fam == "rhs":        # read u, v, w, T, p, Hprev x4; write H x4, R x4
+        return 136 * n, 330 * n
+    if fam == "crank_nicolson":  # four variables: read R, read/write q (algorithmic)
+        return 4 * 24 * n, 4 * 8 * n
+    if fam == "cfl_reduce":
+        return 24 * n, 10 * n
+    return None
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1705_01423_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(fam: str, w):
+    """DRAM bytes per launch group from the committed ncu summary, scaled to the
+    workload; None when missing or taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("src_hash") != src_hash():
+        return None
+    e = d.get("families", {}).get(fam)
+    if not e:
+        return None
+    return e["bytes_per_point"] * w.nx * w.ny * w.nz
+
+
+# ------------------------------------------------------------------ oracle baseline
+def oracle_step_time(nx, ny, nz, steps=1, warmup=0):
+    import torch
+    import synth
+    from oracle import Grid, timestep as ts
+    w = synth.workload("rb512", nx=nx, ny=ny, nz=nz)
+    g = Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces())
+    ph = ts.Phys(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, T_bot=w.T_bot, T_top=w.T_top)
+    st = tuple(torch.as_tensor(a) for a in synth.rb_initial(w, 0))
+    H = None
+    from oracle import operators as op
+    for _ in range(warmup):
+        st, H = ts.step(g, ph, op.cfl_dt(g, st[0], st[1], st[2], w.cfl, w.dt_max), st, H)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        dt = op.cfl_dt(g, st[0], st[1], st[2], w.cfl, w.dt_max)
+        st, H = ts.step(g, ph, dt, st, H)
+        times.append(time.perf_counter() - t0)
+    return times, torch.get_num_threads()
+
+
+# ------------------------------------------------------------------ main (ours)
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_1705_01423_gb300 import Context, Physics
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = synth.workload(args.workload)
+    ph = Physics(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, u_bot=w.u_bot, u_top=w.u_top,
+                 T_bot=w.T_bot, T_top=w.T_top)
+    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), phys=ph)
+    if w.has_T:
+        host = synth.rb_initial(w, seed=rank)
+    else:
+        u0, v0, w0, p0 = synth.couette_initial(w, seed=rank)
+        host = (u0, v0, w0, None, p0)
+    S = [torch.as_tensor(a).to(dev) if a is not None else None for a in host]
+    H = [torch.zeros_like(S[0]), torch.zeros_like(S[1]), torch.zeros_like(S[2]),
+         torch.zeros_like(S[3]) if S[3] is not None else None]
+
+    def step():
+        ctx.cfl(S[0], S[1], S[2], w.cfl, w.dt_max)
+        for l in range(3):
+            ctx.rk3_substep(l, -1.0, *S, *H)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ctx.profile(True)
+    ctx.profile_read()
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = ctx.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    launches = ctx.kernel_launches() - l0
+    fams = ctx.profile_read()
+    ctx.profile(False)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    ms_step = ms / args.steps
+    pts = w.nx * w.ny * w.nz
+    value = pts * world * args.steps / (ms / 1e3)
+    # state sanity: still divergence free
+    mdiv = float(ctx.max_divergence(S[0], S[1], S[2]))
+
+    # ---- roofline of the dominant kernel family
+    peaks, peak_src = measured_peaks()
+    top = max((f for f in fams if family_work(f, w)), key=lambda f: fams[f][0])
+    tms, tn = fams[top]
+    per_launch_ms = tms / max(tn, 1)
+    bytes_, flops = family_work(top, w)
+    t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
+    t_alu = flops / (FP64_PEAK_TFLOPS * 1e12)
+    if t_alu > t_hbm:
+        ach = flops / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(top, w),
+                "kernel": top, "launch_ms": per_launch_ms,
+                "peak_source": "FP64 dense: 2 FMA/clk/SM x 152 SMs x 2070 MHz (derived; FMA-chain probe measured 1.19 TFLOP/s at 1995 MHz)",
+                "hbm_frac_of_measured": (bytes_ / (per_launch_ms / 1e3) / 1e9) / peaks["hbm_gbs"]}
+    else:
+        ach = bytes_ / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": traffic_for(top, w), "kernel": top,
+                "launch_ms": per_launch_ms, "peak_source": peak_src}
+    fam_report = {f: {"ms_per_step": v[0] / args.steps, "launch_groups_per_step": v[1] / args.steps,
+                      "share": v[0] / max(sum(x[0] for x in fams.values()), 1e-9)}
+                  for f, v in fams.items() if v[1]}
+
+    # ---- end to end with host buffers (same metric through the API)
+    e2e = None
+    if rank == 0 or world > 1:
+        hS = [torch.as_tensor(a).pin_memory() if a is not None else None for a in host]
+        oS = [torch.empty_like(a).pin_memory() if a is not None else None for a in hS]
+        bi = sum(a.numel() * 8 for a in hS if a is not None)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        k2 = max(2, min(args.steps, 5))
+        barrier()
+        torch.cuda.synchronize()
+        e2.record(stream)
+        for _ in range(k2):
+            for d_, h_ in zip(S, hS):
+                if d_ is not None:
+                    d_.copy_(h_, non_blocking=True)
+            step()
+            for o_, d_ in zip(oS, S):
+                if d_ is not None:
+                    o_.copy_(d_, non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        ems = e2.elapsed_time(e3)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t)
+        e2e = {"value": pts * world * k2 / (ems / 1e3), "unit": "grid-points/s", "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bi, "steps": k2}
+
+    # ---- side measurements: Poisson solve alone, FP64 vs mixed
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra = side_measurements(ctx, w, dev)
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ts_, thr = oracle_step_time(128, 128, w.nz, steps=1)
+        cpu = {"value": 128 * 128 * w.nz / ts_[0], "unit": "grid-points/s", "cores": thr,
+               "kind": "oracle", "host_cpus": os.cpu_count(),
+               "sample": "one FP64 oracle RK3 step (CFL + 3 substeps) of the same Rayleigh-Benard "
+                         "workload on 128x128x%d cells (1/16 of the horizontal points), %.1f s" % (w.nz, ts_[0])}
+
+    if rank == 0:
+        out = {
+            "metric": "grid-points/s per FP64 RK3/CN time step (Rayleigh-Benard Ra=1e8, 512x512x384)",
+            "value": value, "unit": "grid-points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: conduction profile T = 1 - z plus seeded U(-1e-3, 1e-3) noise, velocity 0 at start",
+            "config": {"workload": "rb512: Rayleigh-Benard Ra=1e8 Pr=1 aspect 1, %dx%dx%d cells, tanh-stretched z (s=1.5), "
+                                   "FP64 RK3/CN step = CFL + 3 x (explicit terms, 4 CN sweeps, pressure correction)"
+                                   % (w.nx, w.ny, w.nz),
+                       "l2": "inputs larger than L2 (805 MB per field), no flush needed",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "kernel_families": fam_report, "max_div_after": mdiv, "extra": extra,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def timed(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def side_measurements(ctx, w, dev):
+    """Poisson solve alone on the same grid: FP64 direct vs mixed FP32 + FP64
+    refinement, with the mixed error against the FP64 GPU solve."""
+    import torch
+    import synth
+    from paper_1705_01423_gb300 import Context
+    stream = torch.cuda.current_stream()
+    pts = w.nx * w.ny * w.nz
+    b = torch.as_tensor(synth.noise((w.nz, w.ny, w.nx), seed=123)).to(dev)
+    phi64 = torch.empty_like(b)
+    ms64 = timed(lambda: ctx.poisson_solve(b, phi64), 5, stream)
+    out = {"poisson_fp64": {"ms": ms64, "grid_points_per_s": pts / (ms64 / 1e3)}}
+    try:
+        mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=1e-12,
+                       refine_max_iter=6, poisson_only=True)
+        phim = torch.empty_like(b)
+        _, info = mctx.poisson_solve(b, phim, info=True)
+        msm = timed(lambda: mctx.poisson_solve(b, phim), 5, stream)
+        err = float((phim - phi64).norm() / phi64.norm())
+        out["poisson_mixed"] = {"ms": msm, "grid_points_per_s": pts / (msm / 1e3), "iters": info["iters"],
+                                "rel_l2_vs_fp64_gpu": err, "err_estimate": info["err_estimate"],
+                                "speedup_vs_fp64": ms64 / msm}
+        mctx.profile(True)
+        mctx.profile_read()
+        mctx.poisson_solve(b, phim)
+        out["poisson_mixed"]["families_ms"] = {k: v[0] for k, v in mctx.profile_read().items() if v[1]}
+        mctx.close()
+    except Exception as e:  # report, do not hide
+        out["poisson_mixed"] = {"error": str(e)}
+    ctx.profile(True)
+    ctx.profile_read()
+    ctx.poisson_solve(b, phi64)
+    out["poisson_fp64"]["families_ms"] = {k: v[0] for k, v in ctx.profile_read().items() if v[1]}
+    ctx.profile(False)
+    return out
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The oracle (plain FP64 PyTorch CPU) as the reference arm: each step is one
+    oracle RK3 step of the same workload on a bounded 64x64 x nz sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    w = synth.workload(args.workload)
+    nx = ny = 64
+    times, thr = oracle_step_time(nx, ny, w.nz, steps=args.steps, warmup=args.warmup)
+    tot = sum(times)
+    pts = nx * ny * w.nz
+    value = pts * len(times) / tot
+    out = {"impl": "reference",
+           "metric": "grid-points/s per FP64 RK3/CN time step (Rayleigh-Benard Ra=1e8, 512x512x384)",
+           "value": value, "unit": "grid-points/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "rb512 (oracle on a bounded %dx%dx%d sample per step)" % (nx, ny, w.nz)},
+           "cpu_baseline": {"value": value, "unit": "grid-points/s", "cores": thr, "kind": "oracle",
+                            "sample": "each step: one FP64 oracle RK3 step on %dx%dx%d cells of the Rayleigh-Benard workload" % (nx, ny, w.nz)},
+           "e2e": {"value": value, "unit": "grid-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

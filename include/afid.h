@@ -78,7 +78,8 @@ typedef struct {
 
 typedef struct {
   int iters;               /* refinement iterations used (1 for AFID_FP64)           */
-  double rel_residual;     /* mixed: final ||r||_2/||b||_2; FP64: 0                  */
+  double rel_residual;     /* mixed: ||r||_2/||b - mean||_2 of the residual computed
+                              before the last correction; FP64: 0                   */
   double rhs_mean;         /* cell-volume-weighted mean removed from the rhs         */
   double rhs_absmax;       /* max |rhs|                                              */
   double max_div;          /* afid_project / substep: max |D u| after projection     */
@@ -169,6 +170,20 @@ const char* afid_status_string(afid_status s);
 
 /* Number of kernels launched by this context since creation (instrumentation). */
 long long afid_kernel_launches(const afid_ctx* ctx);
+
+/* Instrumentation: when on, every launch group of the context is bracketed by
+ * CUDA events on its stream, accumulated per kernel family (r2c_x, fft_y,
+ * thomas, zero_mode, c2r_x, project, rhs, crank_nicolson, cfl_reduce, refine,
+ * adjoint; AFID_KERNEL_FAMILIES of them). The first enable creates the event
+ * pool (host-side CUDA events, no device memory). */
+#define AFID_KERNEL_FAMILIES 11
+afid_status afid_profile_enable(afid_ctx* ctx, int on);
+/* Synchronises the stream and returns, per family, the milliseconds and the
+ * number of launch groups recorded since the last read (arrays of n entries,
+ * either may be NULL), then resets the counters. Returns AFID_ERR_INVALID_ARG
+ * if the event pool overflowed (read more often). */
+afid_status afid_profile_read(afid_ctx* ctx, double* ms, long long* launches, int n);
+const char* afid_kernel_family_name(int family);
 
 #ifdef __cplusplus
 }

@@ -79,7 +79,11 @@ _SIGS = {
     "afid_rk3_substep_adjoint": (I, [P, I, D, P, P, P, P, P, P, P, P, P, P, P, P, P]),
     "afid_status_string": (C.c_char_p, [I]),
     "afid_kernel_launches": (C.c_longlong, [P]),
+    "afid_profile_enable": (I, [P, I]),
+    "afid_profile_read": (I, [P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), I]),
+    "afid_kernel_family_name": (C.c_char_p, [I]),
 }
+KERNEL_FAMILIES = 11
 
 
 def lib():
@@ -195,6 +199,17 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(lib().afid_kernel_launches(self._h))
+
+    def profile(self, on=True):
+        _check(lib().afid_profile_enable(self._h, 1 if on else 0), "afid_profile_enable")
+
+    def profile_read(self):
+        """{family: (ms, launch groups)} since the last read (synchronises)."""
+        n = KERNEL_FAMILIES
+        ms = (C.c_double * n)()
+        cnt = (C.c_longlong * n)()
+        _check(lib().afid_profile_read(self._h, ms, cnt, n), "afid_profile_read")
+        return {lib().afid_kernel_family_name(i).decode(): (ms[i], int(cnt[i])) for i in range(n)}
 
     # ---- forward calls
     def poisson_solve(self, rhs, phi=None, info=False):

@@ -90,7 +90,7 @@ size_t spec_elems(const afid_grid_desc* d) {
 void free_all(afid_ctx* c) {
   void* ps[] = {c->metric_buf, c->twx64, c->twy64, c->twx32, c->twy32, c->mtab64, c->mtab32,
                 c->lamx, c->lamy, c->spec, c->phi, c->res, c->bbuf, c->R[0], c->R[1], c->R[2],
-                c->R[3], c->cntab, c->pa32, c->pc32, c->low_modes, c->low_scratch, c->scal,
+                c->R[3], c->cntab, c->pa32, c->pc32, c->lowslot, c->low_scratch, c->scal,
                 c->part, c->part2};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -106,7 +106,7 @@ afid_status fill_info(afid_ctx* c, afid_info* info, bool mixed, bool want_div) {
   info->rhs_absmax = amax;
   if (mixed) {
     info->iters = (int)s[S_ITERS];
-    info->rel_residual = s[S_BNORM2] > 0.0 ? std::sqrt(s[S_RNORM2] / s[S_BNORM2]) : 0.0;
+    info->rel_residual = s[S_BNORM2] > 0.0 ? std::sqrt(s[S_RNORM2] / s[S_BNORM2]) : 0.0;  // before the last correction
     info->err_estimate = s[S_ERREST];
     info->rhs_mean = s[S_BMEAN];
   } else {
@@ -219,7 +219,8 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
 
   // ---- host metric (wall-normal)
   std::vector<double> dzc(nz), rdzc(nz), dzf(nz + 1), rdzf(nz + 1), pa(nz, 0.0), pc(nz, 0.0),
-      ca(nz), cc(nz), fa(nz + 1, 0.0), fc(nz + 1, 0.0), wlo(nz + 1, 0.0), whi(nz + 1, 0.0);
+      ca(nz), cc(nz), fa(nz + 1, 0.0), fc(nz + 1, 0.0), wlo(nz + 1, 0.0), whi(nz + 1, 0.0),
+      pdiag(nz);
   const double* zf = desc->zf;
   for (int k = 0; k < nz; ++k) {
     dzc[k] = zf[k + 1] - zf[k];
@@ -235,13 +236,14 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     ca[k] = 1.0 / (dzc[k] * dzf[k]);
     cc[k] = 1.0 / (dzc[k] * dzf[k + 1]);
   }
+  for (int k = 0; k < nz; ++k) pdiag[k] = pa[k] + pc[k] + 2.0 * g.rdx2 + 2.0 * g.rdy2;
   for (int k = 1; k < nz; ++k) {
     fa[k] = 1.0 / (dzf[k] * dzc[k - 1]);
     fc[k] = 1.0 / (dzf[k] * dzc[k]);
     wlo[k] = dzc[k - 1] / (2.0 * dzf[k]);
     whi[k] = dzc[k] / (2.0 * dzf[k]);
   }
-  const std::vector<double>* arrs[] = {&dzc, &rdzc, &dzf, &rdzf, &pa, &pc, &ca, &cc, &fa, &fc, &wlo, &whi};
+  const std::vector<double>* arrs[] = {&dzc, &rdzc, &dzf, &rdzf, &pa, &pc, &ca, &cc, &fa, &fc, &wlo, &whi, &pdiag};
   std::vector<double> flat;
   std::vector<size_t> offs;
   for (auto* a : arrs) {
@@ -269,18 +271,18 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     const double s = 2.0 * std::sin(M_PI * k / ny) / g.dy;
     lamy[k] = s * s;
   }
-  std::vector<int2> low;
+  std::vector<int> lowslot;
   if (mixed) {
     const double lmin = std::fmin(lamx[1], lamy[1]);
     c->lam_thr = 64.0 * lmin;
+    lowslot.assign((size_t)ny * (M + 1), -1);
     for (int ky = 0; ky < ny; ++ky) {
       const int kyh = ky < ny - ky ? ky : ny - ky;
       for (int kx = 0; kx <= M; ++kx) {
         if (kx == 0 && ky == 0) continue;
-        if (lamx[kx] + lamy[kyh] < c->lam_thr) low.push_back(make_int2(ky, kx));
+        if (lamx[kx] + lamy[kyh] < c->lam_thr) lowslot[(size_t)ky * (M + 1) + kx] = c->nlow++;
       }
     }
-    c->nlow = (int)low.size();
   }
 
   // ---- device allocations
@@ -304,10 +306,8 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     c->bbuf = A.get<double>(n);
     c->pa32 = A.get<float>(nz);
     c->pc32 = A.get<float>(nz);
-    if (c->nlow) {
-      c->low_modes = A.get<int2>(c->nlow);
-      c->low_scratch = A.get<double2>((size_t)c->nlow * nz);
-    }
+    c->lowslot = A.get<int>((size_t)ny * (M + 1));
+    if (c->nlow) c->low_scratch = A.get<double2>((size_t)c->nlow * nz);
   }
   if (!(c->flags & AFID_POISSON_ONLY)) {
     c->R[0] = A.get<double>(n);
@@ -318,7 +318,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   c->cntab = A.get<double>((size_t)3 * 4 * (nz + 1));
   c->scal = A.get<double>(S_COUNT);
   c->part_len = c->num_sms * 8;
-  c->part = A.get<double>(c->part_len);
+  c->part = A.get<double>((size_t)3 * c->part_len);
   if (mixed) {
     c->part2_len = c2r_blocks(g);
     c->part2 = A.get<double>((size_t)2 * c->part2_len);
@@ -330,7 +330,8 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   }
   const double* mb = static_cast<const double*>(c->metric_buf);
   c->m = Metric{mb + offs[0], mb + offs[1], mb + offs[2], mb + offs[3], mb + offs[4], mb + offs[5],
-                mb + offs[6], mb + offs[7], mb + offs[8], mb + offs[9], mb + offs[10], mb + offs[11]};
+                mb + offs[6], mb + offs[7], mb + offs[8], mb + offs[9], mb + offs[10], mb + offs[11],
+                mb + offs[12]};
   bool ok = true;
   auto up = [&](void* dst, const void* src, size_t bytes) {
     if (dst && bytes) ok = ok && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -350,7 +351,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     }
     up(c->pa32, pa32.data(), nz * sizeof(float));
     up(c->pc32, pc32.data(), nz * sizeof(float));
-    if (c->nlow) up(c->low_modes, low.data(), low.size() * sizeof(int2));
+    up(c->lowslot, lowslot.data(), lowslot.size() * sizeof(int));
   }
   ok = ok && cudaMemset(c->spec, 0, se * (mixed ? sizeof(float2) : sizeof(double2))) == cudaSuccess;
   ok = ok && cudaMemset(c->scal, 0, S_COUNT * sizeof(double)) == cudaSuccess;
@@ -370,6 +371,10 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
 afid_status afid_destroy(afid_ctx* c) {
   if (!c) return AFID_ERR_INVALID_ARG;
   cudaStreamSynchronize(c->stream);
+  if (c->prof) {
+    for (cudaEvent_t e : c->prof->ev) cudaEventDestroy(e);
+    delete c->prof;
+  }
   free_all(c);
   delete c;
   return AFID_OK;
@@ -382,6 +387,49 @@ afid_status afid_set_stream(afid_ctx* c, void* stream) {
 }
 
 long long afid_kernel_launches(const afid_ctx* c) { return c ? c->launches : -1; }
+
+afid_status afid_profile_enable(afid_ctx* c, int on) {
+  if (!c) return AFID_ERR_INVALID_ARG;
+  if (!c->prof) {
+    c->prof = new (std::nothrow) Prof;
+    if (!c->prof) return AFID_ERR_OOM;
+    const int n = 1 << 15;
+    c->prof->ev.resize(n);
+    c->prof->fam.resize(n / 2);
+    for (int i = 0; i < n; ++i)
+      if (cudaEventCreate(&c->prof->ev[i]) != cudaSuccess) return AFID_ERR_CUDA;
+  }
+  c->prof->on = on != 0;
+  return AFID_OK;
+}
+
+afid_status afid_profile_read(afid_ctx* c, double* ms, long long* launches, int n) {
+  if (!c || !c->prof || n < 0) return AFID_ERR_INVALID_ARG;
+  Prof* p = c->prof;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFID_ERR_CUDA;
+  for (int i = 0; i + 1 < p->used; i += 2) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]) != cudaSuccess) return AFID_ERR_CUDA;
+    p->ms[p->fam[i / 2]] += t;
+    p->n[p->fam[i / 2]] += 1;
+  }
+  p->used = 0;
+  for (int f = 0; f < n && f < KF_COUNT; ++f) {
+    if (ms) ms[f] = p->ms[f];
+    if (launches) launches[f] = p->n[f];
+    p->ms[f] = 0.0;
+    p->n[f] = 0;
+  }
+  const bool of = p->overflow;
+  p->overflow = false;
+  return of ? AFID_ERR_INVALID_ARG : AFID_OK;
+}
+
+const char* afid_kernel_family_name(int f) {
+  static const char* names[] = {"r2c_x", "fft_y", "thomas", "zero_mode", "c2r_x", "project",
+                                "rhs", "crank_nicolson", "cfl_reduce", "refine", "adjoint"};
+  return (f >= 0 && f < KF_COUNT) ? names[f] : "unknown";
+}
 
 afid_status afid_poisson_solve(afid_ctx* c, const double* rhs, double* phi, afid_info* info) {
   if (!c) return AFID_ERR_INVALID_ARG;

@@ -17,8 +17,10 @@ namespace afid {
 //   fa, fc               [nz+1]   face operator on interior faces k = 1..nz-1
 //   wlo, whi             [nz+1]   volume weights of the cell->face interpolation
 //                                 (dzc[k-1], dzc[k]) / (2 dzf[k]) on interior faces
+//   pdiag                [nz]     pa + pc + 2/dx^2 + 2/dy^2
 struct Metric {
   const double *dzc, *rdzc, *dzf, *rdzf, *pa, *pc, *ca, *cc, *fa, *fc, *wlo, *whi;
+  const double* pdiag;  // [nz] pa + pc + 2/dx^2 + 2/dy^2 (minus the 7-point diagonal)
 };
 
 // Small device-resident scalars (one allocation).
@@ -39,7 +41,35 @@ enum Scalar {
   S_DPREV2,        // mixed: ||delta||_2^2 of the correction before it
   S_PHINORM2,      // mixed: ||phi||_2^2 after the last correction
   S_ERREST,        // mixed: estimated relative error of phi
-  S_COUNT = 16
+  S_D1NORM2,       // mixed: ||d_1||^2 (the first correction, a proxy for ||phi||^2)
+  S_PHIMEAN,       // mixed: weighted mean of phi after the last correction
+  S_COUNT = 20
+};
+
+// Kernel families for the event-based instrumentation (afid_profile_*).
+enum KFam {
+  KF_R2C = 0,   // forward x transform (+ fused divergence)
+  KF_FFTY,      // y transforms, forward and inverse
+  KF_THOMAS,    // Thomas sweeps (incl. FP64 low modes)
+  KF_ZERO,      // exact (0,0) mode
+  KF_C2R,       // inverse x transform
+  KF_PROJECT,   // projection / pressure update / divergence
+  KF_RHS,       // RK3 explicit terms
+  KF_CN,        // Crank-Nicolson tables and sweeps
+  KF_CFL,       // CFL reduction
+  KF_REFINE,    // mixed-precision residual, norms, checks
+  KF_ADJ,       // adjoint-only kernels
+  KF_COUNT
+};
+
+struct Prof {
+  bool on = false;
+  bool overflow = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> fam;  // family of each recorded begin event
+  int used = 0;          // events recorded (begin/end pairs)
+  double ms[KF_COUNT] = {};
+  long long n[KF_COUNT] = {};
 };
 
 struct Grid {
@@ -85,10 +115,11 @@ struct afid_ctx {
   double* bbuf;   // mixed: FP64 right-hand side kept for the residual [nz][ny][nx]
   double* R[4];   // substep right-hand sides (u, v: cells; w, T: faces)
   double* cntab;  // Crank-Nicolson factor tables [3][4][nz+1]
-  // mixed precision: FP32 copies of the Poisson off-diagonals, the low-mode list
-  // (ky, kx) solved in FP64 and its FP64 scratch column
+  // mixed precision: FP32 copies of the Poisson off-diagonals, the slot of every
+  // low mode solved in FP64 (lowslot[ky][kx], -1 otherwise) and its FP64
+  // scratch columns [nz][nlow]
   float *pa32, *pc32;
-  int2* low_modes;
+  int* lowslot;
   int nlow;
   double2* low_scratch;
   double* scal;   // device scalars (Scalar enum)
@@ -98,6 +129,7 @@ struct afid_ctx {
   int part2_len;
   size_t bytes;
   long long launches;
+  afid::Prof* prof;
 };
 
 namespace afid {
@@ -143,6 +175,31 @@ __host__ __device__ inline double rk_rho(int l) { return l == 0 ? 0.0 : (l == 1 
 __host__ __device__ inline double rk_alpha(int l) { return rk_gamma(l) + rk_rho(l); }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Brackets the launches of one kernel family with CUDA events on the context's
+// stream when instrumentation is on (no effect otherwise).
+struct ProfScope {
+  afid_ctx* c;
+  int fam;
+  bool rec;
+  ProfScope(afid_ctx* ctx, int f) : c(ctx), fam(f), rec(false) {
+    Prof* p = c->prof;
+    if (p && p->on && p->used + 2 <= (int)p->ev.size()) {
+      cudaEventRecord(p->ev[p->used], c->stream);
+      p->fam[p->used / 2] = fam;
+      rec = true;
+    } else if (p && p->on) {
+      p->overflow = true;
+    }
+  }
+  ~ProfScope() {
+    if (rec) {
+      Prof* p = c->prof;
+      cudaEventRecord(p->ev[p->used + 1], c->stream);
+      p->used += 2;
+    }
+  }
+};
 
 // Ordered bit pattern of a non-negative double for atomicMax.
 __device__ __forceinline__ unsigned long long dbl_key(double v) {

@@ -32,6 +32,7 @@ __global__ void k_scale_cells(Grid g, Metric m, const double* __restrict__ in,
 }
 
 cudaError_t scale_cells(afid_ctx* c, const double* in, double* out, bool mul) {
+  ProfScope ps(c, KF_ADJ);
   int bx;
   dim3 grd = pgrid(c->g, bx);
   k_scale_cells<<<grd, bx, 0, c->stream>>>(c->g, c->m, in, out, mul ? 1 : 0);
@@ -81,6 +82,7 @@ __global__ void k_adj_proj_post(Grid g, Metric m, double* __restrict__ gu, doubl
 
 cudaError_t project_adjoint_pre(afid_ctx* c, double* gu, double* gv, double* gw, const double* gp,
                                 double, double) {
+  ProfScope ps(c, KF_ADJ);
   int bx;
   dim3 grd = pgrid(c->g, bx);
   k_adj_proj_pre<<<grd, bx, 0, c->stream>>>(c->g, c->m, gu, gv, gw, gp, c->scal, c->phi);
@@ -90,6 +92,7 @@ cudaError_t project_adjoint_pre(afid_ctx* c, double* gu, double* gv, double* gw,
 
 cudaError_t project_adjoint_post(afid_ctx* c, double* gu, double* gv, double* gw, double*,
                                  const double* psi, double, double) {
+  ProfScope ps(c, KF_ADJ);
   int bx;
   dim3 grd = pgrid(c->g, bx);
   k_adj_proj_post<<<grd, bx, 0, c->stream>>>(c->g, c->m, gu, gv, gw, psi, c->scal);
@@ -353,6 +356,7 @@ cudaError_t adjoint_explicit(afid_ctx* c, int l, double dt, const double* u, con
                              const double* w, const double* T, double* gu, double* gv, double* gw,
                              double* gT, double* gp, double* gHu, double* gHv, double* gHw,
                              double* gHT) {
+  ProfScope ps(c, KF_ADJ);
   const Grid& g = c->g;
   int bx;
   dim3 grd = pgrid(g, bx);

@@ -68,6 +68,7 @@ __global__ void k_project(Grid g, Metric m, double* __restrict__ u, double* __re
 }
 
 cudaError_t project(afid_ctx* c, double* u, double* v, double* w, double* p, const double* phi) {
+  ProfScope ps(c, KF_PROJECT);
   int bx;
   dim3 grd = point_grid(c->g, c->g.nz, bx);
   k_project<<<grd, bx, 0, c->stream>>>(c->g, c->m, u, v, w, p, phi, c->scal);
@@ -81,6 +82,7 @@ __global__ void k_set_proj(double* scal, double s, double beta) {
 }
 
 cudaError_t set_proj_scalars(afid_ctx* c, double s, double beta) {
+  ProfScope ps(c, KF_PROJECT);
   k_set_proj<<<1, 1, 0, c->stream>>>(c->scal, s, beta);
   c->launches++;
   return cudaGetLastError();
@@ -100,6 +102,7 @@ __global__ void k_div(Grid g, Metric m, const double* __restrict__ u, const doub
 }
 
 cudaError_t divergence_to(afid_ctx* c, const double* u, const double* v, const double* w, double* b) {
+  ProfScope ps(c, KF_PROJECT);
   int bx;
   dim3 grd = point_grid(c->g, c->g.nz, bx);
   k_div<<<grd, bx, 0, c->stream>>>(c->g, c->m, u, v, w, b, c->scal);
@@ -130,6 +133,7 @@ __global__ void k_maxdiv(Grid g, Metric m, const double* __restrict__ u,
 
 cudaError_t max_divergence(afid_ctx* c, const double* u, const double* v, const double* w,
                            double* out_dev) {
+  ProfScope ps(c, KF_CFL);
   cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double), c->stream);
   if (e) return e;
   k_maxdiv<<<c->num_sms * 8, 256, 0, c->stream>>>(c->g, c->m, u, v, w,
@@ -169,6 +173,7 @@ __global__ void k_cfl_final(double* scal, double cfl, double dt_max, double* cfl
 
 cudaError_t cfl(afid_ctx* c, const double* u, const double* v, const double* w, double cflv,
                 double dt_max, double* cflm_dev) {
+  ProfScope ps(c, KF_CFL);
   cudaError_t e = cudaMemsetAsync(c->scal + S_CFLM, 0, sizeof(double), c->stream);
   if (e) return e;
   k_cfl<<<c->num_sms * 8, 256, 0, c->stream>>>(c->g, c->m, u, v, w,
@@ -307,6 +312,7 @@ __global__ void __launch_bounds__(128) k_rhs(Grid g, Metric m, PhysK ph, int l, 
 cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const double* v,
                          const double* w, const double* T, const double* p, double* Hu,
                          double* Hv, double* Hw, double* HT) {
+  ProfScope ps(c, KF_RHS);
   int bx;
   dim3 grd = point_grid(c->g, c->g.nz, bx);
   PhysK ph{c->phys.nu, c->phys.kappa, c->phys.buoyancy, c->phys.u_bot, c->phys.u_top};
@@ -355,6 +361,7 @@ __global__ void k_cn_tables(Grid g, Metric m, int l, double dt_in, double* __res
 }
 
 cudaError_t cn_tables(afid_ctx* c, int l, double dt) {
+  ProfScope ps(c, KF_CN);
   k_cn_tables<<<1, 32, 0, c->stream>>>(c->g, c->m, l, dt, c->scal, c->phys.nu, c->phys.kappa,
                                        c->cntab);
   c->launches++;
@@ -413,6 +420,7 @@ __global__ void k_cn_sweep(Grid g, const double* __restrict__ tab, double* R0, d
 }
 
 cudaError_t cn_sweeps(afid_ctx* c, double* u, double* v, double* w, double* T) {
+  ProfScope ps(c, KF_CN);
   const size_t NXY = (size_t)c->g.nx * c->g.ny;
   dim3 grd(ceil_div((long long)NXY, 128), 4);
   k_cn_sweep<false><<<grd, 128, 0, c->stream>>>(c->g, c->cntab, c->R[0], c->R[1], c->R[2], c->R[3],
@@ -422,6 +430,7 @@ cudaError_t cn_sweeps(afid_ctx* c, double* u, double* v, double* w, double* T) {
 }
 
 cudaError_t cn_sweeps_adjoint(afid_ctx* c, double* gu, double* gv, double* gw, double* gT) {
+  ProfScope ps(c, KF_CN);
   const size_t NXY = (size_t)c->g.nx * c->g.ny;
   dim3 grd(ceil_div((long long)NXY, 128), 4);
   k_cn_sweep<true><<<grd, 128, 0, c->stream>>>(c->g, c->cntab, c->R[0], c->R[1], c->R[2], c->R[3],
@@ -431,32 +440,56 @@ cudaError_t cn_sweeps_adjoint(afid_ctx* c, double* gu, double* gv, double* gw, d
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision refinement: weighted mean of b, FP64 residual
-// r = (b - mean) - L phi with per-block partial sums of r^2, and the
-// convergence test. All kernels return at once when converged.
-__global__ void k_wmean_partial(Grid g, Metric m, const double* __restrict__ b, double* part) {
+// Mixed-precision refinement. FP64 statistics of b, FP64 residual
+// r = (b - mean_W b) - L phi, the convergence test on the correction norms,
+// and the final FP64 gauge (zero weighted mean of phi: the residual cannot
+// see a constant, so the FP32 corrections' gauge round-off is removed here).
+__global__ void k_bstats_partial(Grid g, Metric m, const double* __restrict__ b, double* part) {
   const size_t n = (size_t)g.nx * g.ny * g.nz, NXY = (size_t)g.nx * g.ny;
-  double s = 0.0;
+  double sw = 0.0, s1 = 0.0, s2 = 0.0;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x)
-    s += m.dzc[c / NXY] * b[c];
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-__global__ void k_wmean_final(Grid g, Metric m, const double* part, int np, double* scal) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
-  s = block_sum(s);
+       c += (size_t)gridDim.x * blockDim.x) {
+    const double v = b[c];
+    sw += m.dzc[c / NXY] * v;
+    s1 += v;
+    s2 += v * v;
+  }
+  sw = block_sum(sw);
+  s1 = block_sum(s1);
+  s2 = block_sum(s2);
   if (threadIdx.x == 0) {
-    double sw = 0.0;
-    for (int k = 0; k < g.nz; ++k) sw += m.dzc[k];
-    scal[S_BMEAN] = s / (sw * (double)g.nx * (double)g.ny);
-    scal[S_CONVERGED] = 0.0;
-    scal[S_ITERS] = 0.0;
+    part[3 * blockIdx.x] = sw;
+    part[3 * blockIdx.x + 1] = s1;
+    part[3 * blockIdx.x + 2] = s2;
   }
 }
 
+__global__ void k_bstats_final(Grid g, Metric m, const double* part, int np, double* scal) {
+  double sw = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    sw += part[3 * i];
+    s1 += part[3 * i + 1];
+    s2 += part[3 * i + 2];
+  }
+  sw = block_sum(sw);
+  s1 = block_sum(s1);
+  s2 = block_sum(s2);
+  if (threadIdx.x == 0) {
+    double swz = 0.0;
+    for (int k = 0; k < g.nz; ++k) swz += m.dzc[k];
+    const double n = (double)g.nx * (double)g.ny * (double)g.nz;
+    const double mean = sw / (swz * (double)g.nx * (double)g.ny);
+    scal[S_BMEAN] = mean;
+    scal[S_BNORM2] = s2 - 2.0 * mean * s1 + n * mean * mean;
+    scal[S_RNORM2] = scal[S_BNORM2];
+    scal[S_CONVERGED] = 0.0;
+    scal[S_ITERS] = 0.0;
+    scal[S_DNORM2] = 0.0;
+    scal[S_ERREST] = 1.0;
+  }
+}
+
+// r = (b - mean) - L phi, FP64 7-point operator; per-block sum of r^2.
 __global__ void k_residual(Grid g, Metric m, const double* __restrict__ b,
                            const double* __restrict__ phi, double* __restrict__ r, double* part,
                            const double* scal) {
@@ -470,83 +503,110 @@ __global__ void k_residual(Grid g, Metric m, const double* __restrict__ b,
     const size_t rr = c / g.nx;
     const int j = (int)(rr % g.ny), k = (int)(rr / g.ny);
     const double f = phi[c];
-    const double fkm = k > 0 ? phi[c - NXY] : f;
-    const double fkp = k < g.nz - 1 ? phi[c + NXY] : f;
-    const double L = (phi[at(g, k, j, (i + 1) & (g.nx - 1))] - 2.0 * f + phi[at(g, k, j, (i - 1) & (g.nx - 1))]) * g.rdx2 +
-                     (phi[at(g, k, (j + 1) & (g.ny - 1), i)] - 2.0 * f + phi[at(g, k, (j - 1) & (g.ny - 1), i)]) * g.rdy2 +
-                     m.pc[k] * (fkp - f) - m.pa[k] * (f - fkm);
+    const double sx = phi[at(g, k, j, (i + 1) & (g.nx - 1))] + phi[at(g, k, j, (i - 1) & (g.nx - 1))];
+    const double sy = phi[at(g, k, (j + 1) & (g.ny - 1), i)] + phi[at(g, k, (j - 1) & (g.ny - 1), i)];
+    double L = sx * g.rdx2;
+    L = fma(sy, g.rdy2, L);
+    if (k < g.nz - 1) L = fma(m.pc[k], phi[c + NXY], L);
+    if (k > 0) L = fma(m.pa[k], phi[c - NXY], L);
+    L = fma(-m.pdiag[k], f, L);
     const double rv = (b[c] - mean) - L;
     r[c] = rv;
-    s += rv * rv;
+    s = fma(rv, rv, s);
   }
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// Convergence test of the refinement. The residual norm is recorded for the
-// report; the stopping rule uses the corrections: with linear convergence the
-// error left after correction k is about ||d_k|| (||d_k|| / ||d_{k-1}||), and
-// the iteration stops once that estimate is below tol ||phi||. (A residual
-// test alone under-estimates the error by up to the condition number of L.)
-__global__ void k_refine_check(const double* part, int np, const double* part2, int np2,
-                               double* scal, double tol, int first) {
+// Convergence test after correction k (iterations counted here). The stopping
+// rule uses the correction norms: with linear convergence the error left after
+// correction k >= 3 is about ||d_k|| (||d_k|| / ||d_{k-1}||), after correction
+// 2 at most ||d_2||; ||d_1|| stands for ||phi||. (A residual test alone
+// under-estimates the error by up to the condition number of L.) Also records
+// the weighted mean of phi and the norm of the residual computed before this
+// correction.
+__global__ void k_refine_check(Grid g, Metric m, const double* part, int np, const double* part2,
+                               int np2, double* scal, double tol) {
   if (scal[S_CONVERGED] != 0.0) return;
-  double s = 0.0, d2 = 0.0, f2 = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
-  if (!first)
-    for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-      d2 += part2[2 * i];
-      f2 += part2[2 * i + 1];
-    }
-  s = block_sum(s);
+  double d2 = 0.0, ps = 0.0, rs = 0.0;
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+    d2 += part2[2 * i];
+    ps += part2[2 * i + 1];
+  }
+  const bool have_r = scal[S_ITERS] > 0.5;
+  if (have_r)
+    for (int i = threadIdx.x; i < np; i += blockDim.x) rs += part[i];
   d2 = block_sum(d2);
-  f2 = block_sum(f2);
+  ps = block_sum(ps);
+  rs = block_sum(rs);
   if (threadIdx.x == 0) {
-    scal[S_RNORM2] = s;
-    if (first) {
-      scal[S_BNORM2] = s;
-      if (s == 0.0) scal[S_CONVERGED] = 1.0;
-      return;
-    }
+    double swz = 0.0;
+    for (int k = 0; k < g.nz; ++k) swz += m.dzc[k];
+    scal[S_PHIMEAN] = ps / (swz * (double)g.nx * (double)g.ny);
+    if (have_r) scal[S_RNORM2] = rs;
     scal[S_ITERS] += 1.0;
-    const double prev = scal[S_ITERS] > 1.0 ? scal[S_DNORM2] : d2;
+    const double k = scal[S_ITERS];
+    const double prev = scal[S_DNORM2];
+    if (k < 1.5) scal[S_D1NORM2] = d2;
+    const double ref = scal[S_D1NORM2];
+    double est2;
+    if (k < 1.5) est2 = d2;
+    else if (k < 2.5) est2 = d2;
+    else est2 = prev > 0.0 ? d2 * d2 / prev : 0.0;
     scal[S_DPREV2] = prev;
     scal[S_DNORM2] = d2;
-    scal[S_PHINORM2] = f2;
-    const double est2 = prev > 0.0 ? d2 * d2 / prev : 0.0;  // (||d_k||^2 / ||d_{k-1}||)^2
-    scal[S_ERREST] = f2 > 0.0 ? sqrt(est2 / f2) : 0.0;
-    if (s == 0.0 || est2 <= tol * tol * f2) scal[S_CONVERGED] = 1.0;
+    scal[S_ERREST] = ref > 0.0 ? sqrt(est2 / ref) : 0.0;
+    if (d2 == 0.0 || (k > 1.5 && est2 <= tol * tol * ref)) scal[S_CONVERGED] = 1.0;
   }
 }
 
-cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, const double* skip);
+__global__ void k_sub_mean(Grid g, double* __restrict__ phi, const double* __restrict__ scal) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  const double pm = scal[S_PHIMEAN];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x)
+    phi[c] -= pm;
+}
+
+cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, const double* skip,
+                                bool first);
 
 // Mixed-precision refined solve (device-side convergence test, no host sync):
-//   mean = mean_W(b); phi = 0; r = b - mean; ||b - mean||^2
-//   repeat refine_max_iter times (every kernel returns at once once converged):
-//     phi += FP32-spectral-solve(r); r = b - mean - L phi (FP64); converged when
-//     the estimated error ||d_k||^2 / ||d_{k-1}|| <= tol ||phi|| (k_refine_check).
+//   stats of b (mean_W b, ||b - mean||^2)
+//   k = 1: phi = FP32-solve(b)
+//   k = 2..max: r = (b - mean) - L phi (FP64), phi += FP32-solve(r)
+//   after every correction: convergence test on the correction norms
+//   finally phi -= mean_W(phi) in FP64.
+// Every kernel returns at once once the test has passed.
 cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi) {
   const Grid& g = c->g;
-  const size_t n = (size_t)g.nx * g.ny * g.nz;
   const int nb = c->part_len;
   cudaError_t e;
-  k_wmean_partial<<<nb, 256, 0, c->stream>>>(g, c->m, b, c->part);
-  k_wmean_final<<<1, 1024, 0, c->stream>>>(g, c->m, c->part, nb, c->scal);
-  c->launches += 2;
-  if ((e = cudaMemsetAsync(phi, 0, n * sizeof(double), c->stream))) return e;
-  k_residual<<<nb, 256, 0, c->stream>>>(g, c->m, b, phi, c->res, c->part, c->scal);
-  k_refine_check<<<1, 1024, 0, c->stream>>>(c->part, nb, c->part2, c->part2_len, c->scal, c->tol, 1);
-  c->launches += 2;
-  if ((e = cudaGetLastError())) return e;
-  for (int it = 0; it < c->max_iter; ++it) {
-    if ((e = spectral_solve_fp32(c, c->res, phi, c->scal + S_CONVERGED))) return e;
-    k_residual<<<nb, 256, 0, c->stream>>>(g, c->m, b, phi, c->res, c->part, c->scal);
-    k_refine_check<<<1, 1024, 0, c->stream>>>(c->part, nb, c->part2, c->part2_len, c->scal, c->tol, 0);
+  {
+    ProfScope ps(c, KF_REFINE);
+    k_bstats_partial<<<nb, 256, 0, c->stream>>>(g, c->m, b, c->part);
+    k_bstats_final<<<1, 1024, 0, c->stream>>>(g, c->m, c->part, nb, c->scal);
     c->launches += 2;
     if ((e = cudaGetLastError())) return e;
   }
-  return cudaSuccess;
+  for (int it = 0; it < c->max_iter; ++it) {
+    if (it > 0) {
+      ProfScope ps(c, KF_REFINE);
+      k_residual<<<nb, 256, 0, c->stream>>>(g, c->m, b, phi, c->res, c->part, c->scal);
+      c->launches++;
+    }
+    if ((e = spectral_solve_fp32(c, it == 0 ? b : c->res, phi, c->scal + S_CONVERGED, it == 0)))
+      return e;
+    ProfScope ps(c, KF_REFINE);
+    k_refine_check<<<1, 1024, 0, c->stream>>>(g, c->m, c->part, nb, c->part2, c->part2_len,
+                                              c->scal, c->tol);
+    c->launches++;
+    if ((e = cudaGetLastError())) return e;
+  }
+  ProfScope ps(c, KF_REFINE);
+  k_sub_mean<<<nb, 256, 0, c->stream>>>(g, phi, c->scal);
+  c->launches++;
+  return cudaGetLastError();
 }
 
 }  // namespace afid

@@ -157,8 +157,9 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
 // O'_k = (X_k - conj X_{M-k}) conj(w_k); an inverse M-point FFT gives
 // nx (x_2n + i x_2n+1) before the 1/(nx ny) normalisation `scale`.
 // ACC = 0 writes phi, ACC = 1 adds to phi.
-template <typename R, int ACC>
-__global__ void __launch_bounds__(512) k_c2r_x(Grid g, const typename cplx<R>::T* __restrict__ spec,
+template <typename R, int MODE>
+__global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
+                                               const typename cplx<R>::T* __restrict__ spec,
                                                const typename cplx<R>::T* __restrict__ tw,
                                                double scale, double* __restrict__ phi,
                                                const double* __restrict__ skip,
@@ -197,32 +198,41 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, const typename cplx<R>::T
   }
   __syncthreads();
   fft_line<true>(buf, M, tw, 2, t, active);
-  double d2 = 0.0, f2 = 0.0;
+  R d2 = (R)0;
+  double psum = 0.0;
   if (active) {
     double2* o2 = reinterpret_cast<double2*>(phi + (size_t)row * g.nx);
+    const R sc = (R)scale;
     for (int n = t; n < M; n += T) {
       const C z = buf[pad8(n)];
-      double2 r = make_double2((double)z.x * scale, (double)z.y * scale);
-      if (ACC) {
-        d2 += r.x * r.x + r.y * r.y;
-        const double2 old = o2[n];
-        r.x += old.x;
-        r.y += old.y;
-        f2 += r.x * r.x + r.y * r.y;
+      if (MODE == 0) {
+        o2[n] = make_double2((double)z.x * scale, (double)z.y * scale);
+      } else {
+        const R dx = z.x * sc, dy = z.y * sc;
+        d2 += dx * dx + dy * dy;
+        double2 r = make_double2((double)dx, (double)dy);
+        if (MODE == 1) {
+          const double2 old = o2[n];
+          r.x += old.x;
+          r.y += old.y;
+        }
+        psum += r.x + r.y;
+        o2[n] = r;
       }
-      o2[n] = r;
     }
+    psum *= m.dzc[row / g.ny];
   }
-  if (ACC && part) {
-    // per-block ||delta||^2 and ||phi||^2 for the refinement's convergence test
-    __shared__ double red[2][8];
+  if (MODE != 0) {
+    // per-block ||delta||^2 and sum of dzc * phi (weighted mean of phi)
+    __shared__ double red[2][16];
+    double dd = (double)d2;
     for (int o = 16; o > 0; o >>= 1) {
-      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-      f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+      dd += __shfl_xor_sync(0xffffffffu, dd, o);
+      psum += __shfl_xor_sync(0xffffffffu, psum, o);
     }
     if ((threadIdx.x & 31) == 0) {
-      red[0][threadIdx.x >> 5] = d2;
-      red[1][threadIdx.x >> 5] = f2;
+      red[0][threadIdx.x >> 5] = dd;
+      red[1][threadIdx.x >> 5] = psum;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -313,35 +323,65 @@ __global__ void __launch_bounds__(128) k_thomas(Grid g, Metric m, typename cplx<
   }
 }
 
-// FP64 sweeps for the listed low modes of an FP32 spectral array (mixed
-// precision): the nearly singular systems are eliminated in FP64, the
-// intermediate d' kept in an FP64 scratch column [nz][nlow].
-__global__ void k_thomas_low(Grid g, Metric m, float2* __restrict__ spec,
-                             const double* __restrict__ mtab, const int2* __restrict__ modes,
-                             int nlow, double2* __restrict__ scratch,
-                             const double* __restrict__ skip) {
+// Mixed precision: FP32 sweeps for most modes; the nearly singular low modes
+// (lowslot[ky][kx] >= 0) are eliminated in FP64 with the FP64 pivot table,
+// their intermediate d' kept in an FP64 scratch column [nz][nlow].
+__global__ void __launch_bounds__(128) k_thomas_mixed(Grid g, Metric m, float2* __restrict__ spec,
+                                                      const float* __restrict__ mtab32,
+                                                      const double* __restrict__ mtab64,
+                                                      const float* __restrict__ pa32,
+                                                      const float* __restrict__ pc32,
+                                                      const int* __restrict__ lowslot, int nlow,
+                                                      double2* __restrict__ scratch,
+                                                      const double* __restrict__ skip) {
   if (skip && *skip != 0.0) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nlow) return;
-  const int ky = modes[s].x, kx = modes[s].y;
-  const int kyh = min(ky, g.ny - ky);
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ky = blockIdx.y;
   const int W = g.M + 1;
+  if (kx >= W || (kx == 0 && ky == 0)) return;
+  const int kyh = min(ky, g.ny - ky);
   const size_t plane = (size_t)g.ny * g.P;
   const size_t tplane = (size_t)g.nyh * W;
   float2* col = spec + (size_t)ky * g.P + kx;
-  const double* mt = mtab + (size_t)kyh * W + kx;
+  const int nz = g.nz;
+  const int slot = lowslot[(size_t)ky * W + kx];
+  if (slot < 0) {
+    const float* mt = mtab32 + (size_t)kyh * W + kx;
+    float2 d = col[0];
+    float mk = mt[0];
+    float2 dp = make_float2(d.x * mk, d.y * mk);
+    col[0] = dp;
+#pragma unroll 4
+    for (int k = 1; k < nz; ++k) {
+      d = col[k * plane];
+      mk = mt[k * tplane];
+      const float ak = pa32[k];
+      dp = make_float2((d.x - ak * dp.x) * mk, (d.y - ak * dp.y) * mk);
+      col[k * plane] = dp;
+    }
+    float2 x = dp;
+#pragma unroll 4
+    for (int k = nz - 2; k >= 0; --k) {
+      const float2 e = col[k * plane];
+      const float cp = pc32[k] * mt[k * tplane];
+      x = make_float2(e.x - cp * x.x, e.y - cp * x.y);
+      col[k * plane] = x;
+    }
+    return;
+  }
+  const double* mt = mtab64 + (size_t)kyh * W + kx;
   double2 dp = make_double2(0.0, 0.0);
-  for (int k = 0; k < g.nz; ++k) {
+  for (int k = 0; k < nz; ++k) {
     const float2 d = col[k * plane];
     const double mk = mt[k * tplane];
     const double ak = m.pa[k];
     dp = make_double2(((double)d.x - ak * dp.x) * mk, ((double)d.y - ak * dp.y) * mk);
-    scratch[(size_t)k * nlow + s] = dp;
+    scratch[(size_t)k * nlow + slot] = dp;
   }
   double2 x = dp;
-  col[(size_t)(g.nz - 1) * plane] = make_float2((float)x.x, (float)x.y);
-  for (int k = g.nz - 2; k >= 0; --k) {
-    const double2 e = scratch[(size_t)k * nlow + s];
+  col[(size_t)(nz - 1) * plane] = make_float2((float)x.x, (float)x.y);
+  for (int k = nz - 2; k >= 0; --k) {
+    const double2 e = scratch[(size_t)k * nlow + slot];
     const double cp = m.pc[k] * mt[k * tplane];
     x = make_double2(e.x - cp * x.x, e.y - cp * x.y);
     col[k * plane] = make_float2((float)x.x, (float)x.y);
@@ -405,6 +445,7 @@ static size_t line_smem(int N) {
 template <typename R>
 static cudaError_t run_fft_y(afid_ctx* c, typename cplx<R>::T* spec, const typename cplx<R>::T* tw,
                              bool inv, const double* skip) {
+  ProfScope ps(c, KF_FFTY);
   const Grid& g = c->g;
   const size_t ls = line_smem<R>(g.ny);
   // widest tile that keeps a block within 1024 threads and ~112 KB of shared memory
@@ -435,6 +476,7 @@ static cudaError_t run_r2c(afid_ctx* c, const double* rhs, const double* u, cons
                            const double* w, bool dev_s, typename cplx<R>::T* spec,
                            const typename cplx<R>::T* tw, int want_stats, const double* skip) {
   const double scale = 1.0;
+  ProfScope ps(c, KF_R2C);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
   const size_t sm = (size_t)lines * line_smem<R>(g.M);
@@ -456,16 +498,17 @@ static cudaError_t run_r2c(afid_ctx* c, const double* rhs, const double* u, cons
 
 template <typename R>
 static cudaError_t run_c2r(afid_ctx* c, const typename cplx<R>::T* spec,
-                           const typename cplx<R>::T* tw, double* phi, bool acc,
+                           const typename cplx<R>::T* tw, double* phi, int mode,
                            const double* skip, double* part) {
+  ProfScope ps(c, KF_C2R);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
   const size_t sm = (size_t)lines * line_smem<R>(g.M);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   const double scale = 1.0 / ((double)g.nx * (double)g.ny);
-  auto kf = acc ? k_c2r_x<R, 1> : k_c2r_x<R, 0>;
+  auto kf = mode == 1 ? k_c2r_x<R, 1> : (mode == 2 ? k_c2r_x<R, 2> : k_c2r_x<R, 0>);
   cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  kf<<<blocks, lines * T, sm, c->stream>>>(g, spec, tw, scale, phi, skip, part);
+  kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, spec, tw, scale, phi, skip, part);
   c->launches++;
   return cudaGetLastError();
 }
@@ -480,46 +523,49 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
   if ((e = run_r2c<double>(c, rhs, u, v, w, dev_s, spec, c->twx64, want_stats, nullptr))) return e;
   if ((e = run_fft_y<double>(c, spec, c->twy64, false, nullptr))) return e;
   {
+    ProfScope ps(c, KF_THOMAS);
     dim3 grd(ceil_div(g.M + 1, 128), g.ny);
     k_thomas<double><<<grd, 128, 0, c->stream>>>(g, c->m, spec, c->mtab64, c->m.pa, c->m.pc,
                                                  c->lamx, c->lamy, 0.0, nullptr);
     c->launches++;
     if ((e = cudaGetLastError())) return e;
   }
-  k_zero_mode<double><<<1, 256, g.nz * sizeof(double), c->stream>>>(g, c->m, spec, c->scal, nullptr);
+  {
+    ProfScope ps(c, KF_ZERO);
+    k_zero_mode<double><<<1, 256, g.nz * sizeof(double), c->stream>>>(g, c->m, spec, c->scal, nullptr);
+  }
   c->launches++;
   if ((e = cudaGetLastError())) return e;
   if ((e = run_fft_y<double>(c, spec, c->twy64, true, nullptr))) return e;
-  return run_c2r<double>(c, spec, c->twx64, phi, false, nullptr, nullptr);
+  return run_c2r<double>(c, spec, c->twx64, phi, 0, nullptr, nullptr);
 }
 
-// FP32 spectral solve of the residual `src` (FP64) accumulated into phi, used by
-// the mixed-precision refinement; kernels return at once when *skip != 0.
-cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, const double* skip) {
+// FP32 spectral solve of `src` (FP64) for the mixed-precision refinement:
+// phi = delta (first) or phi += delta, with per-block partials of ||delta||^2
+// and of sum dzc phi in c->part2; every kernel returns at once when *skip != 0.
+cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, const double* skip,
+                                bool first) {
   const Grid& g = c->g;
   float2* spec = static_cast<float2*>(c->spec);
   cudaError_t e;
   if ((e = run_r2c<float>(c, src, nullptr, nullptr, nullptr, false, spec, c->twx32, 0, skip))) return e;
   if ((e = run_fft_y<float>(c, spec, c->twy32, false, skip))) return e;
   {
+    ProfScope ps(c, KF_THOMAS);
     dim3 grd(ceil_div(g.M + 1, 128), g.ny);
-    k_thomas<float><<<grd, 128, 0, c->stream>>>(g, c->m, spec, c->mtab32, c->pa32, c->pc32,
-                                                c->lamx, c->lamy, c->lam_thr, skip);
+    k_thomas_mixed<<<grd, 128, 0, c->stream>>>(g, c->m, spec, c->mtab32, c->mtab64, c->pa32,
+                                               c->pc32, c->lowslot, c->nlow, c->low_scratch, skip);
     c->launches++;
     if ((e = cudaGetLastError())) return e;
   }
-  if (c->nlow > 0) {
-    k_thomas_low<<<ceil_div(c->nlow, 64), 64, 0, c->stream>>>(g, c->m, spec, c->mtab64,
-                                                              c->low_modes, c->nlow,
-                                                              c->low_scratch, skip);
-    c->launches++;
-    if ((e = cudaGetLastError())) return e;
+  {
+    ProfScope ps(c, KF_ZERO);
+    k_zero_mode<float><<<1, 256, g.nz * sizeof(double), c->stream>>>(g, c->m, spec, c->scal, skip);
   }
-  k_zero_mode<float><<<1, 256, g.nz * sizeof(double), c->stream>>>(g, c->m, spec, c->scal, skip);
   c->launches++;
   if ((e = cudaGetLastError())) return e;
   if ((e = run_fft_y<float>(c, spec, c->twy32, true, skip))) return e;
-  return run_c2r<float>(c, spec, c->twx32, phi, true, skip, c->part2);
+  return run_c2r<float>(c, spec, c->twx32, phi, first ? 2 : 1, skip, c->part2);
 }
 
 }  // namespace afid
