@@ -185,6 +185,33 @@ afid_status afid_profile_enable(afid_ctx* ctx, int on);
 afid_status afid_profile_read(afid_ctx* ctx, double* ms, long long* launches, int n);
 const char* afid_kernel_family_name(int family);
 
+/* FP64 Poisson solve that allocates nothing. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * that runs under a memory allocator it does not own (a host framework that
+ * reserves the device memory pool), a real-time loop that must never
+ * allocate, or a plugin that has no place to keep a context object. It
+ * computes exactly what afid_poisson_solve computes in AFID_FP64 (same
+ * kernels, same tables) for the grid (nx, ny, nz, lx, ly, zf_host), but
+ * every piece of workspace -- metric, twiddles, wavenumbers, Thomas pivot
+ * table and the spectral array -- lives in one file-scope __device__ array of
+ * AFID_NOALLOC_BYTES (16 MiB) that every GPU loading the library holds until
+ * the process exits. The workspace needed is about
+ *   16 nz ny roundup16(nx/2+1) + 8 nz (ny/2+1)(nx/2+1) bytes (+ small tables),
+ * e.g. 64^3 or 128 x 128 x 64 fit; a grid that does not fit returns
+ * AFID_ERR_UNSUPPORTED_SIZE before anything is launched. The caller passes
+ * the input rhs and the output phi (device, [nz][ny][nx], 16-byte aligned; they
+ * may alias) and a cudaStream_t. The call uploads the tables from a static
+ * host staging buffer and launches on `stream`; it calls no cudaMalloc,
+ * cudaFree or other allocating routine. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture. All calls share the one
+ * array and its contents persist from the last call; calls that overlap on the
+ * GPU (two streams, two host threads) race on it. */
+#define AFID_NOALLOC_BYTES (16u << 20)
+afid_status afid_poisson_solve_noalloc(int nx, int ny, int nz, double lx, double ly,
+                                       const double* zf_host, const double* rhs, double* phi,
+                                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

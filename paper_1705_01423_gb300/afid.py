@@ -82,6 +82,7 @@ _SIGS = {
     "afid_profile_enable": (I, [P, I]),
     "afid_profile_read": (I, [P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), I]),
     "afid_kernel_family_name": (C.c_char_p, [I]),
+    "afid_poisson_solve_noalloc": (I, [I, I, I, D, D, P, P, P, P]),
 }
 KERNEL_FAMILIES = 11
 
