@@ -34,10 +34,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# FP64: 2 FMA per clock per SM on this part (measured 1.19 TFLOP/s at 1995 MHz
-# with an FMA-chain probe), 152 SMs, 2070 MHz maximum SM clock.
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
-FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12
+# FP64 issue rate of this part: 2 FP64 operations (add, multiply or fused
+# multiply-add alike) per clock per SM -- an FMA-chain probe measured 1.19
+# TFLOP/s (FMA = 2 flops) at 1995 MHz on 152 SMs -- at the 2070 MHz maximum
+# SM clock. The ALU roofline below counts FP64 operations, each add, multiply
+# or FMA once, against this issue rate.
+FP64_OPS_PEAK = 2 * 152 * 2.070e9 / 1e12          # 0.629 T FP64 ops/s
 
 
 def parse():
@@ -49,7 +51,18 @@ def parse():
     ap.add_argument("--workload", default="rb512")
     ap.add_argument("--no-extra", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", default=None,
+                    help="override the workload's cells as NXxNYxNZ (profiling smaller cases)")
     return ap.parse_args()
+
+
+def workload_from(args):
+    import synth
+    w = synth.workload(args.workload)
+    if args.grid:
+        nx, ny, nz = (int(t) for t in args.grid.lower().split("x"))
+        w.nx, w.ny, w.nz = nx, ny, nz
+    return w
 
 
 def measured_peaks():
@@ -115,33 +128,52 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ work model
-def family_work(fam: str, w, fp: str = "f64"):
+def fft_ops(n: int) -> float:
+    """FP64 operations per complex point of one n-point transform with the
+    library's pass sequence (radix 8 first, untwiddled, then twiddled radix-8
+    passes, then one radix-4 or radix-2 pass): 7, 10.5, 7, 4 per point."""
+    ops, p = 0.0, 1
+    while n // p >= 8:
+        ops += 7.0 if p == 1 else 10.5
+        p *= 8
+    if n // p == 4:
+        ops += 7.0
+    elif n // p == 2:
+        ops += 4.0
+    return ops
+
+
+def family_work(fam: str, w):
     """Algorithmic work of one launch group of a kernel family on grid w:
-    (bytes, flops). Bytes are the compulsory HBM traffic of the kernel's own
-    inputs and outputs; flops the standard counts (5 N log2 N per complex
-    N-point FFT, 2.5 N log2 N per real one; stencils counted in FP64
-    operations of their definition, FMA = 2)."""
+    (bytes, fp64_ops). Bytes: compulsory HBM traffic of the kernel's own inputs
+    and outputs. FP64 operations: the formulation's arithmetic, each add,
+    multiply or FMA counted once (per grid point unless noted):
+      r2c_x  divergence 7 + packed real FFT fft_ops(nx/2)/2 + unpacking 4
+      c2r_x  packing 4 + fft_ops(nx/2)/2 + scaling 1
+      fft_y  fft_ops(ny) per complex point (nx/2+1 complex per row)
+      thomas 7 per complex point (4 forward, 3 backward)
+      project 12; rhs 120 (u 31, v 28, w 35, T 27); crank_nicolson 16 (4 fields);
+      cfl_reduce 9."""
     nx, ny, nz = w.nx, w.ny, w.nz
     n = nx * ny * nz
     M1 = nx // 2 + 1
-    cs = 16 if fp == "f64" else 8       # complex element
-    rs = 8 if fp == "f64" else 4        # real element in the spectral stages
-    if fam == "r2c_x":      # divergence fused: read u, v, w (8 B each) + write spectrum
-        return 24 * n + cs * M1 * ny * nz, 2.5 * nx * math.log2(nx) * ny * nz + 8 * n
+    nc = M1 * ny * nz
+    if fam == "r2c_x":
+        return 24 * n + 16 * nc, (7 + fft_ops(nx // 2) / 2 + 4) * n
     if fam == "c2r_x":
-        return cs * M1 * ny * nz + 8 * n, 2.5 * nx * math.log2(nx) * ny * nz
+        return 16 * nc + 8 * n, (4 + fft_ops(nx // 2) / 2 + 1) * n
     if fam == "fft_y":
-        return 2 * cs * M1 * ny * nz, 5 * ny * math.log2(ny) * M1 * nz
-    if fam == "thomas":     # data in/out + reciprocal-pivot table, read once
-        return 2 * cs * M1 * ny * nz + rs * M1 * (ny // 2 + 1) * nz, 14 * M1 * ny * nz
-    if fam == "project":    # read phi, u, v, w, p; write u, v, w, p
-        return 72 * n, 20 * n
-    if fam == "rhs":        # read u, v, w, T, p, Hprev x4; write H x4, R x4
-        return 136 * n, 330 * n
-    if fam == "crank_nicolson":  # four variables: read R, read/write q (algorithmic)
-        return 4 * 24 * n, 4 * 8 * n
+        return 32 * nc, fft_ops(ny) * nc
+    if fam == "thomas":
+        return 32 * nc + 8 * M1 * (ny // 2 + 1) * nz, 7 * nc
+    if fam == "project":
+        return 72 * n, 12 * n
+    if fam == "rhs":
+        return 136 * n, 120 * n
+    if fam == "crank_nicolson":
+        return 4 * 24 * n, 16 * n
     if fam == "cfl_reduce":
-        return 24 * n, 10 * n
+        return 24 * n, 9 * n
     return None
 
 
@@ -207,7 +239,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = synth.workload(args.workload)
+    w = workload_from(args)
     ph = Physics(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, u_bot=w.u_bot, u_top=w.u_top,
                  T_bot=w.T_bot, T_top=w.T_top)
     ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), phys=ph)
@@ -268,24 +300,36 @@ def run_ours(args):
     top = max((f for f in fams if family_work(f, w)), key=lambda f: fams[f][0])
     tms, tn = fams[top]
     per_launch_ms = tms / max(tn, 1)
-    bytes_, flops = family_work(top, w)
+    bytes_, ops = family_work(top, w)
     t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
-    t_alu = flops / (FP64_PEAK_TFLOPS * 1e12)
+    t_alu = ops / (FP64_OPS_PEAK * 1e12)
     if t_alu > t_hbm:
-        ach = flops / (per_launch_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(top, w),
+        ach = ops / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_OPS_PEAK, "unit": "TFLOP/s",
+                "frac": ach / FP64_OPS_PEAK, "traffic": traffic_for(top, w),
                 "kernel": top, "launch_ms": per_launch_ms,
-                "peak_source": "FP64 dense: 2 FMA/clk/SM x 152 SMs x 2070 MHz (derived; FMA-chain probe measured 1.19 TFLOP/s at 1995 MHz)",
+                "peak_source": "derived FP64 issue rate: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz (FMA-chain "
+                               "probe: 1.19 TFLOP/s at 1995 MHz); FLOP here = one FP64 add, mul or FMA",
+                "hbm_gbs_algorithmic": bytes_ / (per_launch_ms / 1e3) / 1e9,
                 "hbm_frac_of_measured": (bytes_ / (per_launch_ms / 1e3) / 1e9) / peaks["hbm_gbs"]}
     else:
         ach = bytes_ / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic_for(top, w), "kernel": top,
-                "launch_ms": per_launch_ms, "peak_source": peak_src}
-    fam_report = {f: {"ms_per_step": v[0] / args.steps, "launch_groups_per_step": v[1] / args.steps,
-                      "share": v[0] / max(sum(x[0] for x in fams.values()), 1e-9)}
-                  for f, v in fams.items() if v[1]}
+                "launch_ms": per_launch_ms, "peak_source": peak_src + " copy bandwidth"}
+    fam_report = {}
+    tot_ms = max(sum(x[0] for x in fams.values()), 1e-9)
+    for f, v in fams.items():
+        if not v[1]:
+            continue
+        e = {"ms_per_step": v[0] / args.steps, "launch_groups_per_step": v[1] / args.steps,
+             "share": v[0] / tot_ms}
+        fw = family_work(f, w)
+        if fw:
+            t = v[0] / v[1] / 1e3
+            e["fp64_ops_frac"] = fw[1] / t / 1e12 / FP64_OPS_PEAK
+            e["hbm_frac_algorithmic"] = fw[0] / t / 1e9 / peaks["hbm_gbs"]
+        fam_report[f] = e
 
     # ---- end to end with host buffers (same metric through the API)
     e2e = None
@@ -409,8 +453,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import synth
-    w = synth.workload(args.workload)
+    w = workload_from(args)
     nx = ny = 64
     times, thr = oracle_step_time(nx, ny, w.nz, steps=args.steps, warmup=args.warmup)
     tot = sum(times)

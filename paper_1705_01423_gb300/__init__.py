@@ -5,5 +5,6 @@ include/afid.h); `afid` is its ctypes binding and `autodiff` wraps the
 hand-written adjoints as torch.autograd Functions with a checkpointed rollout.
 """
 from .afid import Context, Physics, AfidError, lib, LIB_PATH, exported_symbols  # noqa: F401
+from . import autodiff  # noqa: F401
 
 __all__ = ["Context", "Physics", "AfidError", "lib", "LIB_PATH", "exported_symbols"]

@@ -184,145 +184,6 @@ cudaError_t cfl(afid_ctx* c, const double* u, const double* v, const double* w, 
 }
 
 // ---------------------------------------------------------------------------
-// Explicit terms H and Crank-Nicolson right-hand sides R of substep l.
-// Thread (i, j, k), k = 0..nz-1, handles u and v at cell k and w and T on
-// face k (k >= 1). Advection is the conservative form with arithmetic face
-// averages; u and v are carried onto z-faces with the volume weights
-// (dzc_{k-1}, dzc_k)/(2 dzf_k).
-struct PhysK {
-  double nu, kappa, buoy, ubot, utop;
-};
-
-__global__ void __launch_bounds__(128) k_rhs(Grid g, Metric m, PhysK ph, int l, double dt_in,
-                                             const double* __restrict__ dt_dev,
-                                             const double* __restrict__ u, const double* __restrict__ v,
-                                             const double* __restrict__ w, const double* __restrict__ T,
-                                             const double* __restrict__ p, double* __restrict__ Hu,
-                                             double* __restrict__ Hv, double* __restrict__ Hw,
-                                             double* __restrict__ HT, double* __restrict__ Ru,
-                                             double* __restrict__ Rv, double* __restrict__ Rw,
-                                             double* __restrict__ RT) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int ip = (i + 1) & (nx - 1), im = (i - 1) & (nx - 1);
-  const int jp = (j + 1) & (ny - 1), jm = (j - 1) & (ny - 1);
-  const size_t NXY = (size_t)nx * ny;
-  const double dt = dt_in > 0.0 ? dt_in : *dt_dev;
-  const double gam = rk_gamma(l), rho = rk_rho(l), alp = rk_alpha(l);
-  const size_t c = at(g, k, j, i);
-  const size_t cim = at(g, k, j, im), cip = at(g, k, j, ip);
-  const size_t cjm = at(g, k, jm, i), cjp = at(g, k, jp, i);
-
-  // ---------------- u at (x-face i, cell j, cell k)
-  const double u0 = u[c], uip = u[cip], uim = u[cim], ujp = u[cjp], ujm = u[cjm];
-  const double v0 = v[c], vim = v[cim], vip = v[cip], vjp = v[cjp], vjm = v[cjm];
-  const double vjpim = v[at(g, k, jp, im)];
-  const double ujmip = u[at(g, k, jm, ip)];
-  const double ukm = k > 0 ? u[c - NXY] : ph.ubot;
-  const double ukp = k < nz - 1 ? u[c + NXY] : ph.utop;
-  const double vkm = k > 0 ? v[c - NXY] : 0.0;
-  const double vkp = k < nz - 1 ? v[c + NXY] : 0.0;
-  const double wk = w[c], wkim = w[cim], wkjm = w[cjm];
-  const double wk1 = w[c + NXY], wk1im = w[cim + NXY], wk1jm = w[cjm + NXY];
-  const double rdzc = m.rdzc[k];
-  {
-    const double ur = 0.5 * (u0 + uip), ul = 0.5 * (uim + u0);
-    const double ax = (ur * ur - ul * ul) * g.rdx;
-    const double cj = 0.25 * (vim + v0) * (ujm + u0);
-    const double cjp1 = 0.25 * (vjpim + vjp) * (u0 + ujp);
-    const double ay = (cjp1 - cj) * g.rdy;
-    const double fzk = k > 0 ? 0.25 * (wkim + wk) * (ukm + u0) : 0.0;
-    const double fzk1 = k < nz - 1 ? 0.25 * (wk1im + wk1) * (u0 + ukp) : 0.0;
-    const double az = (fzk1 - fzk) * rdzc;
-    const double lap = (uip - 2.0 * u0 + uim) * g.rdx2 + (ujp - 2.0 * u0 + ujm) * g.rdy2;
-    const double H = -(ax + ay + az) + ph.nu * lap;
-    const double dzz = m.cc[k] * (ukp - u0) - m.ca[k] * (u0 - ukm);
-    const double gp = (p[c] - p[cim]) * g.rdx;
-    double r = gam * H + alp * (ph.nu * dzz - gp);
-    if (l > 0) r += rho * Hu[c];
-    Hu[c] = H;
-    Ru[c] = dt * r;
-  }
-  // ---------------- v at (cell i, y-face j, cell k)
-  {
-    const double cj = 0.25 * (ujm + u0) * (vim + v0);          // corner (x-face i, y-face j)
-    const double cip1 = 0.25 * (ujmip + uip) * (v0 + vip);     // corner (x-face i+1, y-face j)
-    const double ax = (cip1 - cj) * g.rdx;
-    const double vt = 0.5 * (v0 + vjp), vb = 0.5 * (vjm + v0);
-    const double ay = (vt * vt - vb * vb) * g.rdy;
-    const double fzk = k > 0 ? 0.25 * (wkjm + wk) * (vkm + v0) : 0.0;
-    const double fzk1 = k < nz - 1 ? 0.25 * (wk1jm + wk1) * (v0 + vkp) : 0.0;
-    const double az = (fzk1 - fzk) * rdzc;
-    const double lap = (vip - 2.0 * v0 + vim) * g.rdx2 + (vjp - 2.0 * v0 + vjm) * g.rdy2;
-    const double H = -(ax + ay + az) + ph.nu * lap;
-    const double dzz = m.cc[k] * (vkp - v0) - m.ca[k] * (v0 - vkm);
-    const double gp = (p[c] - p[cjm]) * g.rdy;
-    double r = gam * H + alp * (ph.nu * dzz - gp);
-    if (l > 0) r += rho * Hv[c];
-    Hv[c] = H;
-    Rv[c] = dt * r;
-  }
-  if (k == 0) {  // wall planes of the face arrays: no explicit term, no unknown
-    Hw[c] = 0.0;
-    Hw[c + (size_t)nz * NXY] = 0.0;
-    if (T) {
-      HT[c] = 0.0;
-      HT[c + (size_t)nz * NXY] = 0.0;
-    }
-    return;
-  }
-  // ---------------- w and T on interior z-face k
-  const double wlo = m.wlo[k], whi = m.whi[k], rdzf = m.rdzf[k];
-  const double ufi = wlo * ukm + whi * u0;
-  const double ufip = wlo * u[cip - NXY] + whi * uip;
-  const double vfj = wlo * vkm + whi * v0;
-  const double vfjp = wlo * v[cjp - NXY] + whi * vjp;
-  const double wip = w[cip], wjp = w[cjp], wkm = w[c - NXY];
-  const double wc_k = 0.5 * (wk + wk1), wc_km = 0.5 * (wkm + wk);
-  {
-    const double ax = (ufip * 0.5 * (wk + wip) - ufi * 0.5 * (wkim + wk)) * g.rdx;
-    const double ay = (vfjp * 0.5 * (wk + wjp) - vfj * 0.5 * (wkjm + wk)) * g.rdy;
-    const double az = (wc_k * wc_k - wc_km * wc_km) * rdzf;
-    const double lap = (wip - 2.0 * wk + wkim) * g.rdx2 + (wjp - 2.0 * wk + wkjm) * g.rdy2;
-    double H = -(ax + ay + az) + ph.nu * lap;
-    if (T) H += ph.buoy * T[c];
-    const double dzz = m.fc[k] * (wk1 - wk) - m.fa[k] * (wk - wkm);
-    const double gp = (p[c] - p[c - NXY]) * rdzf;
-    double r = gam * H + alp * (ph.nu * dzz - gp);
-    if (l > 0) r += rho * Hw[c];
-    Hw[c] = H;
-    Rw[c] = dt * r;
-  }
-  if (T) {
-    const double t0 = T[c], tim = T[cim], tip = T[cip], tjm = T[cjm], tjp = T[cjp];
-    const double tkm = T[c - NXY], tkp = T[c + NXY];
-    const double ax = (ufip * 0.5 * (t0 + tip) - ufi * 0.5 * (tim + t0)) * g.rdx;
-    const double ay = (vfjp * 0.5 * (t0 + tjp) - vfj * 0.5 * (tjm + t0)) * g.rdy;
-    const double az = (wc_k * 0.5 * (t0 + tkp) - wc_km * 0.5 * (tkm + t0)) * rdzf;
-    const double lap = (tip - 2.0 * t0 + tim) * g.rdx2 + (tjp - 2.0 * t0 + tjm) * g.rdy2;
-    const double H = -(ax + ay + az) + ph.kappa * lap;
-    const double dzz = m.fc[k] * (tkp - t0) - m.fa[k] * (t0 - tkm);
-    double r = gam * H + alp * ph.kappa * dzz;
-    if (l > 0) r += rho * HT[c];
-    HT[c] = H;
-    RT[c] = dt * r;
-  }
-}
-
-cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const double* v,
-                         const double* w, const double* T, const double* p, double* Hu,
-                         double* Hv, double* Hw, double* HT) {
-  ProfScope ps(c, KF_RHS);
-  int bx;
-  dim3 grd = point_grid(c->g, c->g.nz, bx);
-  PhysK ph{c->phys.nu, c->phys.kappa, c->phys.buoyancy, c->phys.u_bot, c->phys.u_top};
-  k_rhs<<<grd, bx, 0, c->stream>>>(c->g, c->m, ph, l, dt, c->scal + S_DT, u, v, w, T, p, Hu, Hv,
-                                   Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3]);
-  c->launches++;
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Crank-Nicolson factor tables for substep l: operator o = 0 (cells, nu),
 // 1 (faces, nu), 2 (faces, kappa); (I - beta dzz) with beta = alpha_l dt d/2.
 // Row k: sub = -beta a_k, diag = 1 + beta (a_k + c_k), sup = -beta c_k;

@@ -1,0 +1,259 @@
+// Explicit terms H and Crank-Nicolson right-hand sides R of one RK3 substep
+// (Sec. 2.1), z-marching formulation.
+//
+// On this part FP64 issues at 2 instructions per clock per SM, 1/64 of FP32,
+// so the kernel is bound by the number of FP64 instructions per grid point,
+// not by HBM. The conservative advection operator is a difference of face
+// fluxes; here every face flux is computed once and shared:
+//   * z: each thread owns one (x, y) column and walks k upwards, carrying the
+//     flux through face k+1 (cell k for w, T) to the next step in registers;
+//   * x: a warp spans 32 consecutive x; the neighbour's flux comes by shuffle;
+//   * y: the block spans BY rows; fluxes of the neighbouring row come through a
+//     double-buffered shared-memory exchange (one barrier per k).
+// Constant factors (1/2, 1/4, 1/dx, dt gamma_l, ...) are folded, and the
+// Laplacian and wall-normal second differences use precomputed diagonals.
+// Same discretisation as the point-wise formulation it replaces:
+//   u: [(u_i+u_i+1)^2 - (u_i-1+u_i)^2]/(4dx) + [C_i,j+1 - C_i,j]/(4dy)
+//      + [Fz_k+1 - Fz_k]/(4 dzc_k), C_i,j = (v_i-1,j + v_i,j)(u_i,j-1 + u_i,j),
+//      Fz_k = (w_i-1,k + w_i,k)(u_k-1 + u_k) (zero on the walls);
+//   v: symmetric; w, T on face k: x/y fluxes uf (q_i-1 + q_i) with
+//      uf = (dzc_k-1 u_k-1 + dzc_k u_k)/(2 dzf_k), z fluxes at cell centres
+//      (w_k + w_k+1)(q_k + q_k+1)/4.
+#include "afid_internal.cuh"
+
+namespace afid {
+
+struct PhysR {
+  double nu, kappa, buoy, ubot, utop;
+};
+
+template <bool HAS_T, int BY>
+__global__ void __launch_bounds__(32 * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR ph, int l, double dt_in,
+                                                    const double* __restrict__ scal,
+                                                    const double* __restrict__ u,
+                                                    const double* __restrict__ v,
+                                                    const double* __restrict__ w,
+                                                    const double* __restrict__ T,
+                                                    const double* __restrict__ p,
+                                                    double* __restrict__ Hu, double* __restrict__ Hv,
+                                                    double* __restrict__ Hw, double* __restrict__ HT,
+                                                    double* __restrict__ Ru, double* __restrict__ Rv,
+                                                    double* __restrict__ Rw, double* __restrict__ RT) {
+  const int BX = blockDim.x;  // min(32, nx)
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int ip = (i + 1) & (nx - 1), im = (i - 1) & (nx - 1);
+  const int jp = (j + 1) & (ny - 1), jm = (j - 1) & (ny - 1);
+  const size_t NXY = (size_t)nx * ny;
+  const bool first_lane = tx == 0, last_lane = tx == BX - 1;
+  const bool first_row = ty == 0, last_row = ty == BY - 1;
+
+  const double dt = dt_in > 0.0 ? dt_in : scal[S_DT];
+  const double cg = dt * rk_gamma(l), cr = dt * rk_rho(l), ca_ = dt * rk_alpha(l);
+  const double cnu = ca_ * ph.nu, ckap = ca_ * ph.kappa;
+  const double cpx = ca_ * g.rdx, cpy = ca_ * g.rdy;
+  const double qx = 0.25 * g.rdx, qy = 0.25 * g.rdy;  // 1/4 of the inverse spacings
+  const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
+  const double lap0 = 2.0 * (g.rdx2 + g.rdy2);
+
+  // shared y-exchange: [buffer][quantity][row][lane]
+  __shared__ double sx[2][4][BY][32];
+
+  const size_t col = (size_t)j * nx + i;
+  const size_t cim = (size_t)j * nx + im, cip = (size_t)j * nx + ip;
+  const size_t cjm = (size_t)jm * nx + i, cjp = (size_t)jp * nx + i;
+  const size_t cjpim = (size_t)jp * nx + im, cjmip = (size_t)jm * nx + ip;
+
+  // column values carried along k
+  double u0 = u[col], v0 = v[col];
+  double w0 = w[col], wk1 = w[NXY + col];
+  double t0 = HAS_T ? T[col] : 0.0, tk1 = HAS_T ? T[NXY + col] : 0.0;
+  double wim0 = w[cim], wjm0 = w[cjm];  // face k at (i-1), (j-1)
+  double fzu = 0.0, fzv = 0.0;          // u, v z-fluxes through face k (wall: 0)
+  double fzw = 0.0, fzt = 0.0;          // w, T z-fluxes at cell k-1
+  double ukm = ph.ubot, vkm = 0.0;      // u, v at k-1 (wall values at k = 0)
+  double uipkm = 0.0, vjpkm = 0.0;      // u(i+1), v(j+1) at k-1
+  double wkm = 0.0, tkm = 0.0, pkm = 0.0;
+
+  for (int k = 0; k < nz; ++k) {
+    const size_t c = (size_t)k * NXY;
+    const int buf = k & 1;
+    // ---------------------------------------------------------------- loads at plane k
+    const double uip = u[c + cip], uim = u[c + cim], ujp = u[c + cjp], ujm = u[c + cjm];
+    const double vip = v[c + cip], vim = v[c + cim], vjp = v[c + cjp], vjm = v[c + cjm];
+    const double ukp = k < nz - 1 ? u[c + NXY + col] : ph.utop;
+    const double vkp = k < nz - 1 ? v[c + NXY + col] : 0.0;
+    const double wk1im = w[c + NXY + cim], wk1jm = w[c + NXY + cjm];
+    const double p0 = p[c + col];
+
+    // ---------------------------------------------------------------- shared fluxes (cell k)
+    const double C = (vim + v0) * (ujm + u0);        // corner (x-face i, y-face j), x4
+    const double fxu = (u0 + uip) * (u0 + uip);       // u at cell centre i, x4
+    const double fyv = (v0 + vjp) * (v0 + vjp);       // v at cell centre j, x4
+    const double fzu1 = k < nz - 1 ? (wk1im + wk1) * (u0 + ukp) : 0.0;  // face k+1, x4
+    const double fzv1 = k < nz - 1 ? (wk1jm + wk1) * (v0 + vkp) : 0.0;
+    const double wsum = w0 + wk1;                     // 2 w at cell centre k
+    const double fzw1 = wsum * wsum;                  // cell k, x4
+    const double fzt1 = HAS_T ? wsum * (t0 + tk1) : 0.0;
+
+    // face-k quantities (k >= 1): uf, vf and the x/y fluxes of w and T
+    double ufi = 0.0, vfj = 0.0, fxw = 0.0, fyw = 0.0, fxt = 0.0, fyt = 0.0;
+    double wip = 0.0, wjp = 0.0, tip = 0.0, tim = 0.0, tjp = 0.0, tjm = 0.0;
+    if (k > 0) {
+      const double wlo = m.wlo[k], whi = m.whi[k];
+      ufi = fma(wlo, ukm, whi * u0);
+      vfj = fma(wlo, vkm, whi * v0);
+      wip = w[c + cip];
+      wjp = w[c + cjp];
+      fxw = ufi * (wim0 + w0);                        // x-face i, x2
+      fyw = vfj * (wjm0 + w0);                        // y-face j, x2
+      if (HAS_T) {
+        tip = T[c + cip];
+        tim = T[c + cim];
+        tjp = T[c + cjp];
+        tjm = T[c + cjm];
+        fxt = ufi * (tim + t0);
+        fyt = vfj * (tjm + t0);
+      }
+    }
+    // ---------------------------------------------------------------- exchange
+    sx[buf][0][ty][tx] = C;
+    sx[buf][1][ty][tx] = fyv;
+    sx[buf][2][ty][tx] = fyw;
+    sx[buf][3][ty][tx] = fyt;
+    __syncthreads();
+    // x neighbours by shuffle (lane i+1 / i-1 of the same row)
+    const unsigned FULL = 0xffffffffu;
+    double Cip = __shfl_down_sync(FULL, C, 1, BX);
+    double fxum = __shfl_up_sync(FULL, fxu, 1, BX);
+    double fxw1 = __shfl_down_sync(FULL, fxw, 1, BX);
+    double fxt1 = __shfl_down_sync(FULL, fxt, 1, BX);
+    if (last_lane) {
+      Cip = (v0 + vip) * (u[c + cjmip] + uip);
+      if (k > 0) {
+        const double ufip = fma(m.wlo[k], uipkm, m.whi[k] * uip);
+        fxw1 = ufip * (w0 + wip);
+        if (HAS_T) fxt1 = ufip * (t0 + tip);
+      }
+    }
+    if (first_lane) fxum = (uim + u0) * (uim + u0);
+    // y neighbours from shared memory (rows j+1 / j-1 of the block)
+    double Cjp, fyvm, fyw1, fyt1;
+    if (!last_row) {
+      Cjp = sx[buf][0][ty + 1][tx];
+      fyw1 = sx[buf][2][ty + 1][tx];
+      fyt1 = sx[buf][3][ty + 1][tx];
+    } else {
+      Cjp = (v[c + cjpim] + vjp) * (u0 + ujp);
+      fyw1 = 0.0;
+      fyt1 = 0.0;
+      if (k > 0) {
+        const double vfjp = fma(m.wlo[k], vjpkm, m.whi[k] * vjp);
+        fyw1 = vfjp * (w0 + wjp);
+        if (HAS_T) fyt1 = vfjp * (t0 + tjp);
+      }
+    }
+    fyvm = !first_row ? sx[buf][1][ty - 1][tx] : (vjm + v0) * (vjm + v0);
+
+    // ---------------------------------------------------------------- u, v at cell k
+    const double rdzc = m.rdzc[k];
+    const double qz = 0.25 * rdzc;
+    {
+      const double A = (fxu - fxum) * qx + (Cjp - C) * qy + (fzu1 - fzu) * qz;
+      const double lap = fma(ujp + ujm, g.rdy2, (uip + uim) * g.rdx2) - lap0 * u0;
+      const double H = fma(ph.nu, lap, -A);
+      const double dzz = fma(m.cc[k], ukp, m.ca[k] * ukm) - (m.cc[k] + m.ca[k]) * u0;
+      double r = fma(cg, H, fma(cnu, dzz, -cpx * (p0 - p[c + cim])));
+      if (l > 0) r = fma(cr, Hu[c + col], r);
+      Hu[c + col] = H;
+      Ru[c + col] = r;
+    }
+    {
+      const double A = (Cip - C) * qx + (fyv - fyvm) * qy + (fzv1 - fzv) * qz;
+      const double lap = fma(vjp + vjm, g.rdy2, (vip + vim) * g.rdx2) - lap0 * v0;
+      const double H = fma(ph.nu, lap, -A);
+      const double dzz = fma(m.cc[k], vkp, m.ca[k] * vkm) - (m.cc[k] + m.ca[k]) * v0;
+      double r = fma(cg, H, fma(cnu, dzz, -cpy * (p0 - p[c + cjm])));
+      if (l > 0) r = fma(cr, Hv[c + col], r);
+      Hv[c + col] = H;
+      Rv[c + col] = r;
+    }
+    // ---------------------------------------------------------------- w, T on face k
+    if (k == 0) {
+      Hw[col] = 0.0;
+      Hw[(size_t)nz * NXY + col] = 0.0;
+      if (HAS_T) {
+        HT[col] = 0.0;
+        HT[(size_t)nz * NXY + col] = 0.0;
+      }
+    } else {
+      const double rdzf = m.rdzf[k];
+      const double qzf = 0.25 * rdzf;
+      {
+        const double A = (fxw1 - fxw) * hx + (fyw1 - fyw) * hy + (fzw1 - fzw) * qzf;
+        const double lap = fma(wjp + wjm0, g.rdy2, (wip + wim0) * g.rdx2) - lap0 * w0;
+        double H = fma(ph.nu, lap, -A);
+        if (HAS_T) H = fma(ph.buoy, t0, H);
+        const double dzz = fma(m.fc[k], wk1, m.fa[k] * wkm) - (m.fc[k] + m.fa[k]) * w0;
+        double r = fma(cg, H, fma(cnu, dzz, -ca_ * rdzf * (p0 - pkm)));
+        if (l > 0) r = fma(cr, Hw[c + col], r);
+        Hw[c + col] = H;
+        Rw[c + col] = r;
+      }
+      if (HAS_T) {
+        const double A = (fxt1 - fxt) * hx + (fyt1 - fyt) * hy + (fzt1 - fzt) * qzf;
+        const double lap = fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2) - lap0 * t0;
+        const double H = fma(ph.kappa, lap, -A);
+        const double dzz = fma(m.fc[k], tk1, m.fa[k] * tkm) - (m.fc[k] + m.fa[k]) * t0;
+        double r = fma(cg, H, ckap * dzz);
+        if (l > 0) r = fma(cr, HT[c + col], r);
+        HT[c + col] = H;
+        RT[c + col] = r;
+      }
+    }
+    // ---------------------------------------------------------------- carry to k+1
+    fzu = fzu1;
+    fzv = fzv1;
+    fzw = fzw1;
+    fzt = fzt1;
+    ukm = u0;
+    vkm = v0;
+    uipkm = uip;
+    vjpkm = vjp;
+    wkm = w0;
+    tkm = t0;
+    pkm = p0;
+    if (k < nz - 1) {
+      u0 = ukp;
+      v0 = vkp;
+      w0 = wk1;
+      t0 = tk1;
+      wim0 = wk1im;
+      wjm0 = wk1jm;
+      wk1 = w[c + 2 * NXY + col];
+      if (HAS_T) tk1 = T[c + 2 * NXY + col];
+    }
+  }
+}
+
+cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const double* v,
+                         const double* w, const double* T, const double* p, double* Hu,
+                         double* Hv, double* Hw, double* HT) {
+  ProfScope ps(c, KF_RHS);
+  const Grid& g = c->g;
+  constexpr int BY = 8;
+  const int bx = g.nx < 32 ? g.nx : 32;
+  dim3 blk(bx, BY), grd(g.nx / bx, g.ny / BY);
+  PhysR ph{c->phys.nu, c->phys.kappa, c->phys.buoyancy, c->phys.u_bot, c->phys.u_top};
+  if (T)
+    k_rhs_zm<true, BY><<<grd, blk, 0, c->stream>>>(g, c->m, ph, l, dt, c->scal, u, v, w, T, p, Hu, Hv,
+                                                   Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3]);
+  else
+    k_rhs_zm<false, BY><<<grd, blk, 0, c->stream>>>(g, c->m, ph, l, dt, c->scal, u, v, w, T, p, Hu,
+                                                    Hv, Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3]);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace afid
