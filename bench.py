@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--workload", default="rb512")
     ap.add_argument("--no-extra", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--poisson-only", action="store_true",
+                    help="only the Poisson-solve side measurement (FP64 and mixed)")
     ap.add_argument("--grid", default=None,
                     help="override the workload's cells as NXxNYxNZ (profiling smaller cases)")
     return ap.parse_args()
@@ -223,6 +225,17 @@ def oracle_step_time(nx, ny, nz, steps=1, warmup=0):
 
 
 # ------------------------------------------------------------------ main (ours)
+def run_poisson_only(args):
+    import torch
+    import synth
+    from paper_1705_01423_gb300 import Context
+    w = workload_from(args)
+    dev = torch.device("cuda", 0)
+    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), poisson_only=True)
+    out = side_measurements(ctx, w, dev)
+    print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "poisson": out}))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -475,6 +488,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.poisson_only:
+        run_poisson_only(args)
     else:
         run_ours(args)
 

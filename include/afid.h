@@ -57,6 +57,10 @@ typedef enum {
 
 /* flags */
 #define AFID_POISSON_ONLY 1 /* do not allocate the RK3 substep workspace */
+#define AFID_WARP_TRIDIAG 2 /* FP64: solve every (kx, ky) system with the warp-partitioned
+                               solver (chunked Thomas per lane + parallel cyclic reduction
+                               across the warp) instead of one system per thread -- the
+                               variant for long wall-normal columns and few modes */
 
 typedef struct {
   int nx, ny, nz;          /* cells; nx, ny powers of two                            */
@@ -79,7 +83,8 @@ typedef struct {
 typedef struct {
   int iters;               /* refinement iterations used (1 for AFID_FP64)           */
   double rel_residual;     /* mixed: ||r||_2/||b - mean||_2 of the residual computed
-                              before the last correction; FP64: 0                   */
+                              before the last correction (the norms are only
+                              accumulated when afid_info is requested); FP64: 0     */
   double rhs_mean;         /* cell-volume-weighted mean removed from the rhs         */
   double rhs_absmax;       /* max |rhs|                                              */
   double max_div;          /* afid_project / substep: max |D u| after projection     */

@@ -90,7 +90,7 @@ size_t spec_elems(const afid_grid_desc* d) {
 void free_all(afid_ctx* c) {
   void* ps[] = {c->metric_buf, c->twx64, c->twy64, c->twx32, c->twy32, c->mtab64, c->mtab32,
                 c->lamx, c->lamy, c->spec, c->phi, c->res, c->bbuf, c->R[0], c->R[1], c->R[2],
-                c->R[3], c->cntab, c->pa32, c->pc32, c->lowslot, c->low_scratch, c->scal,
+                c->R[3], c->cntab, c->pa32, c->pc32, c->lowslot, c->low_modes, c->low_scratch, c->scal,
                 c->part, c->part2};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -144,7 +144,7 @@ afid_status solve_any(afid_ctx* c, const double* rhs, const double* u, const dou
       return AFID_ERR_CUDA;
     b = c->bbuf;
   }
-  if (mixed_solve(c, b, phi)) return AFID_ERR_CUDA;
+  if (mixed_solve(c, b, phi, stats)) return AFID_ERR_CUDA;
   return AFID_OK;
 }
 
@@ -272,6 +272,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     lamy[k] = s * s;
   }
   std::vector<int> lowslot;
+  std::vector<int2> low;
   if (mixed) {
     const double lmin = std::fmin(lamx[1], lamy[1]);
     c->lam_thr = 64.0 * lmin;
@@ -280,7 +281,10 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
       const int kyh = ky < ny - ky ? ky : ny - ky;
       for (int kx = 0; kx <= M; ++kx) {
         if (kx == 0 && ky == 0) continue;
-        if (lamx[kx] + lamy[kyh] < c->lam_thr) lowslot[(size_t)ky * (M + 1) + kx] = c->nlow++;
+        if (lamx[kx] + lamy[kyh] < c->lam_thr) {
+          lowslot[(size_t)ky * (M + 1) + kx] = c->nlow++;
+          low.push_back(make_int2(ky, kx));
+        }
       }
     }
   }
@@ -307,7 +311,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     c->pa32 = A.get<float>(nz);
     c->pc32 = A.get<float>(nz);
     c->lowslot = A.get<int>((size_t)ny * (M + 1));
-    if (c->nlow) c->low_scratch = A.get<double2>((size_t)c->nlow * nz);
+    if (c->nlow) c->low_modes = A.get<int2>(c->nlow);
   }
   if (!(c->flags & AFID_POISSON_ONLY)) {
     c->R[0] = A.get<double>(n);
@@ -352,6 +356,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     up(c->pa32, pa32.data(), nz * sizeof(float));
     up(c->pc32, pc32.data(), nz * sizeof(float));
     up(c->lowslot, lowslot.data(), lowslot.size() * sizeof(int));
+    if (c->nlow) up(c->low_modes, low.data(), low.size() * sizeof(int2));
   }
   ok = ok && cudaMemset(c->spec, 0, se * (mixed ? sizeof(float2) : sizeof(double2))) == cudaSuccess;
   ok = ok && cudaMemset(c->scal, 0, S_COUNT * sizeof(double)) == cudaSuccess;

@@ -115,11 +115,12 @@ struct afid_ctx {
   double* bbuf;   // mixed: FP64 right-hand side kept for the residual [nz][ny][nx]
   double* R[4];   // substep right-hand sides (u, v: cells; w, T: faces)
   double* cntab;  // Crank-Nicolson factor tables [3][4][nz+1]
-  // mixed precision: FP32 copies of the Poisson off-diagonals, the slot of every
-  // low mode solved in FP64 (lowslot[ky][kx], -1 otherwise) and its FP64
-  // scratch columns [nz][nlow]
+  // mixed precision: FP32 copies of the Poisson off-diagonals; the low modes
+  // solved in FP64 by the warp solver: their list (ky, kx) and a mask
+  // lowslot[ky][kx] (>= 0 for a low mode) that the FP32 sweep skips
   float *pa32, *pc32;
   int* lowslot;
+  int2* low_modes;
   int nlow;
   double2* low_scratch;
   double* scal;   // device scalars (Scalar enum)
@@ -142,7 +143,7 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
                            const double* w, bool dev_s, double* phi, bool want_stats);
 int c2r_blocks(const Grid& g);
 // Mixed-precision refined solve of L phi = b (FP64 b, resident) into phi.
-cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi);
+cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi, bool stats);
 // b = D(u, v, w) / s (s from S_PROJ_S)
 cudaError_t divergence_to(afid_ctx* c, const double* u, const double* v, const double* w, double* b);
 // projection with s, beta read from S_PROJ_S / S_PROJ_BETA

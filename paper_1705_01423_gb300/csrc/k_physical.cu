@@ -115,17 +115,18 @@ cudaError_t divergence_to(afid_ctx* c, const double* u, const double* v, const d
 __global__ void k_maxdiv(Grid g, Metric m, const double* __restrict__ u,
                          const double* __restrict__ v, const double* __restrict__ w,
                          unsigned long long* out) {
-  const size_t n = (size_t)g.nx * g.ny * g.nz;
   double mx = 0.0;
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % g.nx);
-    const size_t r = c / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    const int ip = (i + 1) & (g.nx - 1), jp = (j + 1) & (g.ny - 1);
-    const double d = (u[at(g, k, j, ip)] - u[c]) * g.rdx + (v[at(g, k, jp, i)] - v[c]) * g.rdy +
-                     (w[c + (size_t)g.nx * g.ny] - w[c]) * m.rdzc[k];
-    mx = fmax(mx, fabs(d));
+  // rows (k, j) across blocks, x across threads: no 64-bit division per point
+  for (int row = blockIdx.x; row < g.nz * g.ny; row += gridDim.x) {
+    const int k = row / g.ny, j = row - k * g.ny;
+    const int jp = (j + 1) & (g.ny - 1);
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const size_t c = (size_t)row * g.nx + i;
+      const int ip = (i + 1) & (g.nx - 1);
+      const double d = (u[at(g, k, j, ip)] - u[c]) * g.rdx + (v[at(g, k, jp, i)] - v[c]) * g.rdy +
+                       (w[c + (size_t)g.nx * g.ny] - w[c]) * m.rdzc[k];
+      mx = fmax(mx, fabs(d));
+    }
   }
   mx = warp_max(mx);
   if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, dbl_key(mx));
@@ -147,17 +148,18 @@ cudaError_t max_divergence(afid_ctx* c, const double* u, const double* v, const 
 // floored at 1e-8; dt = min(cfl/cflm, dt_max).
 __global__ void k_cfl(Grid g, Metric m, const double* __restrict__ u, const double* __restrict__ v,
                       const double* __restrict__ w, unsigned long long* out) {
-  const size_t n = (size_t)g.nx * g.ny * g.nz;
   double mx = 0.0;
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % g.nx);
-    const size_t r = c / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    const int ip = (i + 1) & (g.nx - 1), jp = (j + 1) & (g.ny - 1);
-    const double q = fabs(u[c] + u[at(g, k, j, ip)]) * g.rdx + fabs(v[c] + v[at(g, k, jp, i)]) * g.rdy +
-                     fabs(w[c] + w[c + (size_t)g.nx * g.ny]) * m.rdzc[k];
-    mx = fmax(mx, q);
+  for (int row = blockIdx.x; row < g.nz * g.ny; row += gridDim.x) {
+    const int k = row / g.ny, j = row - k * g.ny;
+    const int jp = (j + 1) & (g.ny - 1);
+    const double rz = m.rdzc[k];
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const size_t c = (size_t)row * g.nx + i;
+      const int ip = (i + 1) & (g.nx - 1);
+      const double q = fabs(u[c] + u[at(g, k, j, ip)]) * g.rdx + fabs(v[c] + v[at(g, k, jp, i)]) * g.rdy +
+                       fabs(w[c] + w[c + (size_t)g.nx * g.ny]) * rz;
+      mx = fmax(mx, q);
+    }
   }
   mx = warp_max(mx);
   if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, dbl_key(mx));
@@ -305,15 +307,19 @@ cudaError_t cn_sweeps_adjoint(afid_ctx* c, double* gu, double* gv, double* gw, d
 // r = (b - mean_W b) - L phi, the convergence test on the correction norms,
 // and the final FP64 gauge (zero weighted mean of phi: the residual cannot
 // see a constant, so the FP32 corrections' gauge round-off is removed here).
-__global__ void k_bstats_partial(Grid g, Metric m, const double* __restrict__ b, double* part) {
-  const size_t n = (size_t)g.nx * g.ny * g.nz, NXY = (size_t)g.nx * g.ny;
+__global__ void k_bstats_partial(Grid g, Metric m, const double* __restrict__ b, double* part,
+                                 int stats) {
   double sw = 0.0, s1 = 0.0, s2 = 0.0;
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    const double v = b[c];
-    sw += m.dzc[c / NXY] * v;
-    s1 += v;
-    s2 += v * v;
+  for (int row = blockIdx.x; row < g.nz * g.ny; row += gridDim.x) {
+    const double* br = b + (size_t)row * g.nx;
+    double rs = 0.0;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const double v = br[i];
+      rs += v;
+      if (stats) s2 = fma(v, v, s2);  // norms only for the report
+    }
+    sw = fma(m.dzc[row / g.ny], rs, sw);
+    s1 += rs;
   }
   sw = block_sum(sw);
   s1 = block_sum(s1);
@@ -353,27 +359,31 @@ __global__ void k_bstats_final(Grid g, Metric m, const double* part, int np, dou
 // r = (b - mean) - L phi, FP64 7-point operator; per-block sum of r^2.
 __global__ void k_residual(Grid g, Metric m, const double* __restrict__ b,
                            const double* __restrict__ phi, double* __restrict__ r, double* part,
-                           const double* scal) {
+                           const double* scal, int stats) {
   if (scal[S_CONVERGED] != 0.0) return;
-  const size_t n = (size_t)g.nx * g.ny * g.nz, NXY = (size_t)g.nx * g.ny;
+  const size_t NXY = (size_t)g.nx * g.ny;
   const double mean = scal[S_BMEAN];
   double s = 0.0;
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % g.nx);
-    const size_t rr = c / g.nx;
-    const int j = (int)(rr % g.ny), k = (int)(rr / g.ny);
-    const double f = phi[c];
-    const double sx = phi[at(g, k, j, (i + 1) & (g.nx - 1))] + phi[at(g, k, j, (i - 1) & (g.nx - 1))];
-    const double sy = phi[at(g, k, (j + 1) & (g.ny - 1), i)] + phi[at(g, k, (j - 1) & (g.ny - 1), i)];
-    double L = sx * g.rdx2;
-    L = fma(sy, g.rdy2, L);
-    if (k < g.nz - 1) L = fma(m.pc[k], phi[c + NXY], L);
-    if (k > 0) L = fma(m.pa[k], phi[c - NXY], L);
-    L = fma(-m.pdiag[k], f, L);
-    const double rv = (b[c] - mean) - L;
-    r[c] = rv;
-    s = fma(rv, rv, s);
+  for (int row = blockIdx.x; row < g.nz * g.ny; row += gridDim.x) {
+    const int k = row / g.ny, j = row - k * g.ny;
+    const size_t r0 = (size_t)row * g.nx;
+    const size_t rjp = ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx;
+    const size_t rjm = ((size_t)k * g.ny + ((j - 1) & (g.ny - 1))) * g.nx;
+    const double pc = m.pc[k], pa = m.pa[k], pd = m.pdiag[k];
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const size_t c = r0 + i;
+      const double f = phi[c];
+      const double sx = phi[r0 + ((i + 1) & (g.nx - 1))] + phi[r0 + ((i - 1) & (g.nx - 1))];
+      const double sy = phi[rjp + i] + phi[rjm + i];
+      double L = sx * g.rdx2;
+      L = fma(sy, g.rdy2, L);
+      if (k < g.nz - 1) L = fma(pc, phi[c + NXY], L);
+      if (k > 0) L = fma(pa, phi[c - NXY], L);
+      L = fma(-pd, f, L);
+      const double rv = (b[c] - mean) - L;
+      r[c] = rv;
+      if (stats) s = fma(rv, rv, s);
+    }
   }
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
@@ -403,7 +413,10 @@ __global__ void k_refine_check(Grid g, Metric m, const double* part, int np, con
   if (threadIdx.x == 0) {
     double swz = 0.0;
     for (int k = 0; k < g.nz; ++k) swz += m.dzc[k];
-    scal[S_PHIMEAN] = ps / (swz * (double)g.nx * (double)g.ny);
+    // the first accumulate pass sums dzc * phi (= delta_1) in FP64, later ones
+    // sum dzc * delta_k: the weighted mean of phi accumulates
+    const double dm = ps / (swz * (double)g.nx * (double)g.ny);
+    scal[S_PHIMEAN] = scal[S_ITERS] < 0.5 ? dm : scal[S_PHIMEAN] + dm;
     if (have_r) scal[S_RNORM2] = rs;
     scal[S_ITERS] += 1.0;
     const double k = scal[S_ITERS];
@@ -422,11 +435,16 @@ __global__ void k_refine_check(Grid g, Metric m, const double* part, int np, con
 }
 
 __global__ void k_sub_mean(Grid g, double* __restrict__ phi, const double* __restrict__ scal) {
-  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  const size_t n2 = (size_t)g.nx * g.ny * g.nz / 2;  // nx is even
   const double pm = scal[S_PHIMEAN];
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x)
-    phi[c] -= pm;
+  double2* p2 = reinterpret_cast<double2*>(phi);
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n2;
+       c += (size_t)gridDim.x * blockDim.x) {
+    double2 v = p2[c];
+    v.x -= pm;
+    v.y -= pm;
+    p2[c] = v;
+  }
 }
 
 cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, const double* skip,
@@ -439,13 +457,13 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, con
 //   after every correction: convergence test on the correction norms
 //   finally phi -= mean_W(phi) in FP64.
 // Every kernel returns at once once the test has passed.
-cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi) {
+cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi, bool stats) {
   const Grid& g = c->g;
   const int nb = c->part_len;
   cudaError_t e;
   {
     ProfScope ps(c, KF_REFINE);
-    k_bstats_partial<<<nb, 256, 0, c->stream>>>(g, c->m, b, c->part);
+    k_bstats_partial<<<nb, 256, 0, c->stream>>>(g, c->m, b, c->part, stats ? 1 : 0);
     k_bstats_final<<<1, 1024, 0, c->stream>>>(g, c->m, c->part, nb, c->scal);
     c->launches += 2;
     if ((e = cudaGetLastError())) return e;
@@ -453,7 +471,7 @@ cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi) {
   for (int it = 0; it < c->max_iter; ++it) {
     if (it > 0) {
       ProfScope ps(c, KF_REFINE);
-      k_residual<<<nb, 256, 0, c->stream>>>(g, c->m, b, phi, c->res, c->part, c->scal);
+      k_residual<<<nb, 256, 0, c->stream>>>(g, c->m, b, phi, c->res, c->part, c->scal, stats ? 1 : 0);
       c->launches++;
     }
     if ((e = spectral_solve_fp32(c, it == 0 ? b : c->res, phi, c->scal + S_CONVERGED, it == 0)))

@@ -63,6 +63,37 @@ cudaError_t init_thomas_tables(afid_ctx* c) {
 //   X_k = E_k + w_k O_k,  X_{M-k} = conj(E_k - w_k O_k),  w_k = exp(-2 pi i k/nx).
 enum { MODE_RHS = 0, MODE_DIV = 1 };
 
+// FP64 -> working precision. For FP32 the value is truncated with integer
+// operations (sign, rebiased exponent, top 23 mantissa bits; magnitudes below
+// the FP32 normal range flush to zero, above it saturate) instead of a
+// conversion instruction, which issues on the FP64 pipe; the refinement that
+// consumes the FP32 solve corrects the truncation like any other FP32 error.
+// FP32 -> FP64 widening with integer operations (exact for normal numbers and
+// zero; FP32 subnormals flush to zero).
+template <typename R> __device__ __forceinline__ double to_double(R x) { return (double)x; }
+template <> __device__ __forceinline__ double to_double<float>(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long bits = sign | ((unsigned long long)(e + 896u) << 52) |
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+template <typename R> __device__ __forceinline__ R to_real(double x);
+template <> __device__ __forceinline__ double to_real<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_real<float>(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7ff) - 1023 + 127;
+  const unsigned sign = hi & 0x80000000u;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f7fffffu);
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(sign | ((unsigned)e << 23) | mant);
+}
+
 template <typename R, int MODE>
 __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* __restrict__ src,
                                                const double* __restrict__ u,
@@ -85,6 +116,8 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
   const bool active = row < nrows;
   const int stride = pad8(M) + 1;
   C* buf = sm + line * stride;
+  C* stw = sm + lines * stride;  // twiddle table, nx entries
+  for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
   double amax = 0.0;
   if (active) {
     const int nx = g.nx;
@@ -92,10 +125,12 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
       const double2* s2 = reinterpret_cast<const double2*>(src + (size_t)row * nx);
       for (int n = t; n < M; n += T) {
         double2 x = s2[n];
-        x.x *= scale;
-        x.y *= scale;
+        if (scale != 1.0) {
+          x.x *= scale;
+          x.y *= scale;
+        }
         if (want_stats) amax = fmax(amax, fmax(fabs(x.x), fabs(x.y)));
-        buf[pad8(n)] = C{(R)x.x, (R)x.y};
+        buf[pad8(n)] = C{to_real<R>(x.x), to_real<R>(x.y)};
       }
     } else {
       const int k = row / g.ny, j = row - (row / g.ny) * g.ny;
@@ -124,7 +159,7 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
     }
   }
   __syncthreads();
-  fft_line<false>(buf, M, tw, 2, t, active);
+  fft_line<false>(buf, M, stw, 2, t, active);
   if (active) {
     C* out = spec + (size_t)row * g.P;
     const R half = (R)0.5;
@@ -138,7 +173,7 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
       const C zm = buf[pad8(M - k)];
       const C E = C{(zk.x + zm.x) * half, (zk.y - zm.y) * half};
       const C O = C{(zk.y + zm.y) * half, (zm.x - zk.x) * half};
-      const C wO = cmul(O, tw[k]);
+      const C wO = cmul(O, stw[k]);
       out[k] = cadd(E, wO);
       if (k != M / 2) out[M - k] = cconj(csub(E, wO));
     }
@@ -176,6 +211,8 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
   const bool active = row < nrows;
   const int stride = pad8(M) + 1;
   C* buf = sm + line * stride;
+  C* stw = sm + lines * stride;  // twiddle table, nx entries
+  for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
   if (active) {
     const C* in = spec + (size_t)row * g.P;
     for (int k = t; k <= M; k += T) buf[pad8(k)] = in[k];
@@ -190,15 +227,15 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
       }
       const C a = buf[pad8(k)], b = buf[pad8(M - k)];
       const C E = C{a.x + b.x, a.y - b.y};
-      const C O = cmulc(C{a.x - b.x, a.y + b.y}, tw[k]);
+      const C O = cmulc(C{a.x - b.x, a.y + b.y}, stw[k]);
       // Z'_k = E + i O ; Z'_{M-k} = conj(E) + i conj(O)
       buf[pad8(k)] = C{E.x - O.y, E.y + O.x};
       if (k != M / 2) buf[pad8(M - k)] = C{E.x + O.y, O.x - E.y};
     }
   }
   __syncthreads();
-  fft_line<true>(buf, M, tw, 2, t, active);
-  R d2 = (R)0;
+  fft_line<true>(buf, M, stw, 2, t, active);
+  R d2 = (R)0, dsum = (R)0;
   double psum = 0.0;
   if (active) {
     double2* o2 = reinterpret_cast<double2*>(phi + (size_t)row * g.nx);
@@ -210,17 +247,19 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
       } else {
         const R dx = z.x * sc, dy = z.y * sc;
         d2 += dx * dx + dy * dy;
-        double2 r = make_double2((double)dx, (double)dy);
-        if (MODE == 1) {
+        double2 r = make_double2(to_double(dx), to_double(dy));
+        if (MODE == 1) {        // later corrections are small: their sum in FP32
           const double2 old = o2[n];
           r.x += old.x;
           r.y += old.y;
+          dsum += dx + dy;
+        } else {                // the first correction is the bulk of phi: FP64 sum
+          psum += r.x + r.y;
         }
-        psum += r.x + r.y;
         o2[n] = r;
       }
     }
-    psum *= m.dzc[row / g.ny];
+    psum = (MODE == 1 ? to_double(dsum) : psum) * m.dzc[row / g.ny];
   }
   if (MODE != 0) {
     // per-block ||delta||^2 and sum of dzc * phi (weighted mean of phi)
@@ -262,13 +301,25 @@ __global__ void __launch_bounds__(1024) k_fft_y(Grid g, typename cplx<R>::T* __r
   const int ncol = min(TK, g.M + 1 - kx0);
   const int line = threadIdx.x / T, t = threadIdx.x - line * T;
   const int stride = pad8(Ny) + 1;
+  C* stw = sm + TK * stride;  // twiddle table, ny entries
+  for (int q = threadIdx.x; q < Ny; q += blockDim.x) stw[q] = tw[q];
   C* base = spec + (size_t)z * Ny * g.P + kx0;
-  for (int e = threadIdx.x; e < Ny * TK; e += blockDim.x) {
+  // Ny * TK = 8 * blockDim.x: eight independent loads per thread, all in flight
+  C vals[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = threadIdx.x + q * blockDim.x;
     const int ky = e / TK, c = e - (e / TK) * TK;
-    if (c < ncol) sm[c * stride + pad8(ky)] = base[(size_t)ky * g.P + c];
+    if (c < ncol) vals[q] = base[(size_t)ky * g.P + c];
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = threadIdx.x + q * blockDim.x;
+    const int ky = e / TK, c = e - (e / TK) * TK;
+    if (c < ncol) sm[c * stride + pad8(ky)] = vals[q];
   }
   __syncthreads();
-  fft_line<INV>(sm + line * stride, Ny, tw, 1, t, line < ncol);
+  fft_line<INV>(sm + line * stride, Ny, stw, 1, t, line < ncol);
   for (int e = threadIdx.x; e < Ny * TK; e += blockDim.x) {
     const int ky = e / TK, c = e - (e / TK) * TK;
     if (c < ncol) base[(size_t)ky * g.P + c] = sm[c * stride + pad8(ky)];
@@ -344,47 +395,197 @@ __global__ void __launch_bounds__(128) k_thomas_mixed(Grid g, Metric m, float2* 
   const size_t tplane = (size_t)g.nyh * W;
   float2* col = spec + (size_t)ky * g.P + kx;
   const int nz = g.nz;
-  const int slot = lowslot[(size_t)ky * W + kx];
-  if (slot < 0) {
-    const float* mt = mtab32 + (size_t)kyh * W + kx;
-    float2 d = col[0];
-    float mk = mt[0];
-    float2 dp = make_float2(d.x * mk, d.y * mk);
-    col[0] = dp;
+  if (lowslot[(size_t)ky * W + kx] >= 0) return;  // FP64 warp solver (k_tridiag_warp)
+  const float* mt = mtab32 + (size_t)kyh * W + kx;
+  float2 d = col[0];
+  float mk = mt[0];
+  float2 dp = make_float2(d.x * mk, d.y * mk);
+  col[0] = dp;
 #pragma unroll 4
-    for (int k = 1; k < nz; ++k) {
-      d = col[k * plane];
-      mk = mt[k * tplane];
-      const float ak = pa32[k];
-      dp = make_float2((d.x - ak * dp.x) * mk, (d.y - ak * dp.y) * mk);
-      col[k * plane] = dp;
-    }
-    float2 x = dp;
+  for (int k = 1; k < nz; ++k) {
+    d = col[k * plane];
+    mk = mt[k * tplane];
+    const float ak = pa32[k];
+    dp = make_float2((d.x - ak * dp.x) * mk, (d.y - ak * dp.y) * mk);
+    col[k * plane] = dp;
+  }
+  float2 x = dp;
 #pragma unroll 4
-    for (int k = nz - 2; k >= 0; --k) {
-      const float2 e = col[k * plane];
-      const float cp = pc32[k] * mt[k * tplane];
-      x = make_float2(e.x - cp * x.x, e.y - cp * x.y);
-      col[k * plane] = x;
-    }
-    return;
-  }
-  const double* mt = mtab64 + (size_t)kyh * W + kx;
-  double2 dp = make_double2(0.0, 0.0);
-  for (int k = 0; k < nz; ++k) {
-    const float2 d = col[k * plane];
-    const double mk = mt[k * tplane];
-    const double ak = m.pa[k];
-    dp = make_double2(((double)d.x - ak * dp.x) * mk, ((double)d.y - ak * dp.y) * mk);
-    scratch[(size_t)k * nlow + slot] = dp;
-  }
-  double2 x = dp;
-  col[(size_t)(nz - 1) * plane] = make_float2((float)x.x, (float)x.y);
   for (int k = nz - 2; k >= 0; --k) {
-    const double2 e = scratch[(size_t)k * nlow + slot];
-    const double cp = m.pc[k] * mt[k * tplane];
-    x = make_double2(e.x - cp * x.x, e.y - cp * x.y);
-    col[k * plane] = make_float2((float)x.x, (float)x.y);
+    const float2 e = col[k * plane];
+    const float cp = pc32[k] * mt[k * tplane];
+    x = make_float2(e.x - cp * x.x, e.y - cp * x.y);
+    col[k * plane] = x;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Warp-partitioned FP64 solve of one tridiagonal system per warp (the
+// parallel-cyclic-reduction variant for long columns / few systems): rows
+// a_k x_{k-1} + b_k x_k + c_k x_{k+1} = d_k with the Poisson coefficients
+// a = pa, c = pc, b = -pa - pc - lambda, complex d, k = 0..nz-1.
+//   1. lane l owns rows [s_l, e_l); with its last unknown X_l = x_{e_l - 1}
+//      and X_{l-1} treated as known, its interior rows s_l..e_l-2 are solved
+//      by Thomas for three right-hand sides, x_r = g_r + al_r X_{l-1} + be_r X_l;
+//   2. the last row of each chunk gives one equation in X_{l-1}, X_l, X_{l+1}
+//      (the next lane's first interior row arrives by shuffle): a 32-unknown
+//      tridiagonal system, solved by parallel cyclic reduction over shuffles;
+//   3. each lane reconstructs its interior rows.
+// Used for the nearly singular low modes of the mixed-precision solve: the
+// data column is FP32, the elimination FP64. Scratch: 4 doubles per interior
+// row per lane in shared memory.
+__device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl_up_d(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_dn_d(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
+__host__ __device__ inline int warp_rows(int nz) { return nz < 64 ? 2 : (nz + 31) / 32; }
+// warps per block so that the per-lane scratch (5 doubles per row) stays <= 160 KB
+inline int warps_per_block(int nz) {
+  const size_t per_warp = (size_t)32 * 5 * warp_rows(nz) * sizeof(double);
+  int w = (int)((160u << 10) / per_warp);
+  return w < 1 ? 1 : (w > 4 ? 4 : w);
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(128) k_tridiag_warp(Grid g, Metric m, CT* __restrict__ spec,
+                                                      const int2* __restrict__ modes, int nmodes,
+                                                      const double* __restrict__ lamx,
+                                                      const double* __restrict__ lamy,
+                                                      const double* __restrict__ skip) {
+  using R = decltype(CT::x);
+  if (skip && *skip != 0.0) return;
+  extern __shared__ double wsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mi = blockIdx.x * (blockDim.x >> 5) + warp;
+  // modes == nullptr: every (ky, kx) by index, the singular (0,0) excluded
+  bool have = mi < nmodes;  // warp-uniform
+  const int nz = g.nz;
+  const int L = warp_rows(nz);             // rows per lane (>= 2)
+  const int lanes = (nz + L - 1) / L;      // lanes that own rows (<= 32)
+  const int s = lane * L;
+  const int e = lane < lanes ? min(s + L, nz) : s;
+  double* sg = wsm + (size_t)threadIdx.x * 5 * L;  // per row: g.x, g.y, al, be, c'
+  int ky = 0, kx = 0;
+  if (have) {
+    if (modes) {
+      const int2 md = modes[mi];
+      ky = md.x;
+      kx = md.y;
+    } else {
+      ky = mi / (g.M + 1);
+      kx = mi - ky * (g.M + 1);
+    }
+  }
+  have = have && !(kx == 0 && ky == 0);
+  const bool used = have && lane < lanes;  // owns rows s..e-1 (at least one)
+  const int n_int = used ? e - s - 1 : 0;  // interior rows s..e-2
+  const double lam = have ? lamx[kx] + lamy[min(ky, g.ny - ky)] : 0.0;
+  const size_t plane = (size_t)g.ny * g.P;
+  CT* col = spec + (size_t)ky * g.P + kx;
+  // ---- 1. Thomas on the interior rows with right-hand sides d, -a_s e_first, -c e_last
+  {
+    double cprev = 0.0, gx = 0.0, gy = 0.0, al = 0.0, be = 0.0;
+    for (int q = 0; q < n_int; ++q) {
+      const int r = s + q;
+      const bool last = q == n_int - 1;
+      const double a = m.pa[r];  // a * (previous) vanishes at q = 0: all accumulators are 0
+      const double b = -m.pa[r] - m.pc[r] - lam;
+      const double rinv = 1.0 / (b - a * cprev);
+      const CT d = col[(size_t)r * plane];
+      gx = ((double)d.x - a * gx) * rinv;
+      gy = ((double)d.y - a * gy) * rinv;
+      al = ((q == 0 ? -m.pa[s] : 0.0) - a * al) * rinv;
+      be = ((last ? -m.pc[r] : 0.0) - a * be) * rinv;
+      cprev = last ? 0.0 : m.pc[r] * rinv;
+      double* o = sg + 5 * q;
+      o[0] = gx;
+      o[1] = gy;
+      o[2] = al;
+      o[3] = be;
+      o[4] = cprev;
+    }
+    for (int q = n_int - 2; q >= 0; --q) {
+      double* o = sg + 5 * q;
+      const double* n = o + 5;
+      const double cp = o[4];
+      o[0] -= cp * n[0];
+      o[1] -= cp * n[1];
+      o[2] -= cp * n[2];
+      o[3] -= cp * n[3];
+    }
+  }
+  // first interior row of this lane, needed by the previous lane
+  double fgx = 0.0, fgy = 0.0, fal = 0.0, fbe = 0.0;
+  if (n_int > 0) {
+    fgx = sg[0];
+    fgy = sg[1];
+    fal = sg[2];
+    fbe = sg[3];
+  }
+  const double ngx = shfl_dn_d(fgx, 1), ngy = shfl_dn_d(fgy, 1);
+  const double nal = shfl_dn_d(fal, 1), nbe = shfl_dn_d(fbe, 1);
+  const int nn_int = __shfl_down_sync(0xffffffffu, n_int, 1);
+  // ---- 2. interface equation of row e-1: A X_{l-1} + B X_l + C X_{l+1} = D
+  double A = 0.0, B = 1.0, C = 0.0, Dx = 0.0, Dy = 0.0;
+  if (used) {
+    const int r = e - 1;
+    const double a = m.pa[r], c = m.pc[r];
+    const CT d = col[(size_t)r * plane];
+    Dx = (double)d.x;
+    Dy = (double)d.y;
+    B = -m.pa[r] - m.pc[r] - lam;
+    if (n_int > 0) {  // x_{e-2} = g + al X_{l-1} + be X_l
+      const double* o = sg + 5 * (n_int - 1);
+      A = a * o[2];
+      B += a * o[3];
+      Dx -= a * o[0];
+      Dy -= a * o[1];
+    } else {
+      A = a;
+    }
+    if (lane + 1 < lanes) {  // x_e = next lane's first row
+      if (nn_int > 0) {       // = g' + al' X_l + be' X_{l+1}
+        B += c * nal;
+        C = c * nbe;
+        Dx -= c * ngx;
+        Dy -= c * ngy;
+      } else {
+        C = c;
+      }
+    }
+  }
+  // parallel cyclic reduction of the lane system (unused lanes: identity rows)
+  for (int st = 1; st < 32; st <<= 1) {
+    const double Am = shfl_up_d(A, st), Bm = shfl_up_d(B, st), Cm = shfl_up_d(C, st);
+    const double Dxm = shfl_up_d(Dx, st), Dym = shfl_up_d(Dy, st);
+    const double Ap = shfl_dn_d(A, st), Bp = shfl_dn_d(B, st), Cp = shfl_dn_d(C, st);
+    const double Dxp = shfl_dn_d(Dx, st), Dyp = shfl_dn_d(Dy, st);
+    const bool lo = lane >= st, hi = lane + st < 32;
+    const double k1 = lo ? A / Bm : 0.0;
+    const double k2 = hi ? C / Bp : 0.0;
+    const double nA = lo ? -Am * k1 : 0.0;
+    const double nC = hi ? -Cp * k2 : 0.0;
+    B = B - (lo ? Cm * k1 : 0.0) - (hi ? Ap * k2 : 0.0);
+    Dx = Dx - (lo ? Dxm * k1 : 0.0) - (hi ? Dxp * k2 : 0.0);
+    Dy = Dy - (lo ? Dym * k1 : 0.0) - (hi ? Dyp * k2 : 0.0);
+    A = nA;
+    C = nC;
+  }
+  const double Xx = Dx / B, Xy = Dy / B;
+  double Xmx = shfl_up_d(Xx, 1), Xmy = shfl_up_d(Xy, 1);
+  if (lane == 0) {
+    Xmx = 0.0;
+    Xmy = 0.0;
+  }
+  // ---- 3. reconstruct the interior rows, write the FP32 column
+  if (used) {
+    for (int q = 0; q < n_int; ++q) {
+      const double* o = sg + 5 * q;
+      const double vx = o[0] + o[2] * Xmx + o[3] * Xx;
+      const double vy = o[1] + o[2] * Xmy + o[3] * Xy;
+      col[(size_t)(s + q) * plane] = CT{(R)vx, (R)vy};
+    }
+    col[(size_t)(e - 1) * plane] = CT{(R)Xx, (R)Xy};
   }
 }
 
@@ -453,7 +654,7 @@ static cudaError_t run_fft_y(afid_ctx* c, typename cplx<R>::T* spec, const typen
   while (tk > 1 && ((size_t)tk * ls > 112 * 1024 || tk * (g.ny / 8) > 1024)) tk /= 2;
   dim3 grd(ceil_div(g.M + 1, tk), g.nz);
   const int thr = tk * (g.ny / 8);
-  const size_t sm = (size_t)tk * ls;
+  const size_t sm = (size_t)tk * ls + (size_t)g.ny * sizeof(typename cplx<R>::T);
 #define AFID_FFTY(TKV)                                                                        \
   do {                                                                                        \
     auto kf = inv ? k_fft_y<R, true, TKV> : k_fft_y<R, false, TKV>;                          \
@@ -479,7 +680,7 @@ static cudaError_t run_r2c(afid_ctx* c, const double* rhs, const double* u, cons
   ProfScope ps(c, KF_R2C);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
-  const size_t sm = (size_t)lines * line_smem<R>(g.M);
+  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)g.nx * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   if (rhs) {
     auto kf = k_r2c_x<R, MODE_RHS>;
@@ -503,7 +704,7 @@ static cudaError_t run_c2r(afid_ctx* c, const typename cplx<R>::T* spec,
   ProfScope ps(c, KF_C2R);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
-  const size_t sm = (size_t)lines * line_smem<R>(g.M);
+  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)g.nx * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   const double scale = 1.0 / ((double)g.nx * (double)g.ny);
   auto kf = mode == 1 ? k_c2r_x<R, 1> : (mode == 2 ? k_c2r_x<R, 2> : k_c2r_x<R, 0>);
@@ -522,7 +723,16 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
   cudaError_t e;
   if ((e = run_r2c<double>(c, rhs, u, v, w, dev_s, spec, c->twx64, want_stats, nullptr))) return e;
   if ((e = run_fft_y<double>(c, spec, c->twy64, false, nullptr))) return e;
-  {
+  if (c->flags & AFID_WARP_TRIDIAG) {  // long-column variant: one warp per system
+    ProfScope ps(c, KF_THOMAS);
+    const int nm = g.ny * (g.M + 1), wpb = warps_per_block(g.nz);
+    const size_t wsm = (size_t)32 * wpb * 5 * warp_rows(g.nz) * sizeof(double);
+    cudaFuncSetAttribute(k_tridiag_warp<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+    k_tridiag_warp<double2><<<ceil_div(nm, wpb), 32 * wpb, wsm, c->stream>>>(
+        g, c->m, spec, nullptr, nm, c->lamx, c->lamy, nullptr);
+    c->launches++;
+    if ((e = cudaGetLastError())) return e;
+  } else {
     ProfScope ps(c, KF_THOMAS);
     dim3 grd(ceil_div(g.M + 1, 128), g.ny);
     k_thomas<double><<<grd, 128, 0, c->stream>>>(g, c->m, spec, c->mtab64, c->m.pa, c->m.pc,
@@ -557,6 +767,15 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, con
                                                c->pc32, c->lowslot, c->nlow, c->low_scratch, skip);
     c->launches++;
     if ((e = cudaGetLastError())) return e;
+    if (c->nlow > 0) {
+      const int wpb = warps_per_block(g.nz);
+      const size_t wsm = (size_t)32 * wpb * 5 * warp_rows(g.nz) * sizeof(double);
+      cudaFuncSetAttribute(k_tridiag_warp<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+      k_tridiag_warp<float2><<<ceil_div(c->nlow, wpb), 32 * wpb, wsm, c->stream>>>(
+          g, c->m, spec, c->low_modes, c->nlow, c->lamx, c->lamy, skip);
+      c->launches++;
+      if ((e = cudaGetLastError())) return e;
+    }
   }
   {
     ProfScope ps(c, KF_ZERO);

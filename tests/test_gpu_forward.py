@@ -234,3 +234,17 @@ def test_mixed_reports_not_converged():
     assert info["status"] == 4 and info["iters"] == 1
     ref = poisson.solve(g, cpu(b))
     assert rel_l2(phi, ref) < 1e-3
+
+
+@pytest.mark.parametrize("shape", [(16, 8, 3), (32, 16, 100), (16, 16, 384), (32, 8, 1000)])
+def test_poisson_fp64_warp_partitioned_tridiag(shape):
+    """Every (kx, ky) system through the warp-partitioned solver (chunked Thomas
+    per lane + parallel cyclic reduction over the warp), long columns."""
+    nx, ny, nz = shape
+    w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
+    g = ogrid(w)
+    b = synth.noise(g.cell_shape(), seed=nz)
+    ref = poisson.solve(g, cpu(b))
+    ctx = make_ctx(w, poisson_only=True, warp_tridiag=True)
+    phi = ctx.poisson_solve(gpu(b))
+    assert rel_l2(phi, ref) < TOL64
