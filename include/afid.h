@@ -179,9 +179,9 @@ long long afid_kernel_launches(const afid_ctx* ctx);
 /* Instrumentation: when on, every launch group of the context is bracketed by
  * CUDA events on its stream, accumulated per kernel family (r2c_x, fft_y,
  * thomas, zero_mode, c2r_x, project, rhs, crank_nicolson, cfl_reduce, refine,
- * adjoint; AFID_KERNEL_FAMILIES of them). The first enable creates the event
- * pool (host-side CUDA events, no device memory). */
-#define AFID_KERNEL_FAMILIES 11
+ * adjoint, cn_tables; AFID_KERNEL_FAMILIES of them). The first enable creates
+ * the event pool (host-side CUDA events, no device memory). */
+#define AFID_KERNEL_FAMILIES 12
 afid_status afid_profile_enable(afid_ctx* ctx, int on);
 /* Synchronises the stream and returns, per family, the milliseconds and the
  * number of launch groups recorded since the last read (arrays of n entries,

@@ -85,7 +85,7 @@ _SIGS = {
     "afid_kernel_family_name": (C.c_char_p, [I]),
     "afid_poisson_solve_noalloc": (I, [I, I, I, D, D, P, P, P, P]),
 }
-KERNEL_FAMILIES = 11
+KERNEL_FAMILIES = 12
 
 
 def lib():

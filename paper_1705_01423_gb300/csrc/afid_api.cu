@@ -432,7 +432,8 @@ afid_status afid_profile_read(afid_ctx* c, double* ms, long long* launches, int 
 
 const char* afid_kernel_family_name(int f) {
   static const char* names[] = {"r2c_x", "fft_y", "thomas", "zero_mode", "c2r_x", "project",
-                                "rhs", "crank_nicolson", "cfl_reduce", "refine", "adjoint"};
+                                "rhs", "crank_nicolson", "cfl_reduce", "refine", "adjoint",
+                                "cn_tables"};
   return (f >= 0 && f < KF_COUNT) ? names[f] : "unknown";
 }
 

@@ -55,10 +55,11 @@ enum KFam {
   KF_C2R,       // inverse x transform
   KF_PROJECT,   // projection / pressure update / divergence
   KF_RHS,       // RK3 explicit terms
-  KF_CN,        // Crank-Nicolson tables and sweeps
+  KF_CN,        // Crank-Nicolson sweeps
   KF_CFL,       // CFL reduction
   KF_REFINE,    // mixed-precision residual, norms, checks
   KF_ADJ,       // adjoint-only kernels
+  KF_CNTAB,     // Crank-Nicolson factor tables (one tiny kernel per substep)
   KF_COUNT
 };
 

@@ -224,7 +224,7 @@ __global__ void k_cn_tables(Grid g, Metric m, int l, double dt_in, double* __res
 }
 
 cudaError_t cn_tables(afid_ctx* c, int l, double dt) {
-  ProfScope ps(c, KF_CN);
+  ProfScope ps(c, KF_CNTAB);
   k_cn_tables<<<1, 32, 0, c->stream>>>(c->g, c->m, l, dt, c->scal, c->phys.nu, c->phys.kappa,
                                        c->cntab);
   c->launches++;
