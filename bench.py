@@ -226,13 +226,47 @@ def oracle_step_time(nx, ny, nz, steps=1, warmup=0):
 
 # ------------------------------------------------------------------ main (ours)
 def run_poisson_only(args):
+    """Poisson solve alone on the workload grid: FP64 direct and mixed FP32 +
+    FP64 refinement, contexts created one after the other (the 2048^2 x 1024
+    grid needs about 110 GB for the FP64 context and 132 GB for the mixed one)."""
     import torch
     import synth
     from paper_1705_01423_gb300 import Context
     w = workload_from(args)
     dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    pts = w.nx * w.ny * w.nz
+    if w.name == "poisson2048":
+        bh, _ = synth.manufactured_rhs(w, seed=0)
+        b = torch.from_numpy(bh).to(dev)
+        del bh
+    else:
+        b = torch.as_tensor(synth.noise((w.nz, w.ny, w.nx), seed=123)).to(dev)
+    out = {}
     ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), poisson_only=True)
-    out = side_measurements(ctx, w, dev)
+    phi64 = torch.empty_like(b)
+    ms64 = timed(lambda: ctx.poisson_solve(b, phi64), 5, stream)
+    ctx.profile(True)
+    ctx.profile_read()
+    ctx.poisson_solve(b, phi64)
+    fam64 = {k: v[0] for k, v in ctx.profile_read().items() if v[1]}
+    ctx.close()
+    del ctx
+    torch.cuda.synchronize()
+    out["poisson_fp64"] = {"ms": ms64, "grid_points_per_s": pts / (ms64 / 1e3), "families_ms": fam64}
+    mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=1e-12,
+                   refine_max_iter=6, poisson_only=True)
+    phim = torch.empty_like(b)
+    _, info = mctx.poisson_solve(b, phim, info=True)
+    msm = timed(lambda: mctx.poisson_solve(b, phim), 5, stream)
+    mctx.profile(True)
+    mctx.profile_read()
+    mctx.poisson_solve(b, phim)
+    famm = {k: v[0] for k, v in mctx.profile_read().items() if v[1]}
+    err = float((phim - phi64).norm() / phi64.norm())
+    out["poisson_mixed"] = {"ms": msm, "grid_points_per_s": pts / (msm / 1e3), "iters": info["iters"],
+                            "rel_l2_vs_fp64_gpu": err, "err_estimate": info["err_estimate"],
+                            "speedup_vs_fp64": ms64 / msm, "families_ms": famm}
     print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "poisson": out}))
 
 

@@ -169,3 +169,37 @@ def noise(shape, seed: int, sigma: float = 1.0) -> np.ndarray:
 
 def uniform(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     return rng(seed).uniform(lo, hi, size=shape)
+
+
+def manufactured_rhs(w: Workload, seed: int, noise_sigma: float = 1.0, modes=None, out=None):
+    """Right-hand side of the large Poisson workload: N(0, sigma^2) noise plus the
+    manufactured modes cos(2 pi a x/Lx) cos(2 pi b y/Ly) cos(pi m z) sampled at
+    cell centres (unit amplitude), built one z-slab at a time into `out`
+    ([nz][ny][nx] float64, allocated if None). noise_sigma = 0 gives the modes
+    only. Returns (out, modes)."""
+    nx, ny, nz = w.nx, w.ny, w.nz
+    if modes is None:
+        modes = manufactured_modes(seed + 1000)
+    if out is None:
+        out = np.empty((nz, ny, nx))
+    zf = w.faces()
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    xc = (np.arange(nx) + 0.5) * (w.lx / nx)
+    yc = (np.arange(ny) + 0.5) * (w.ly / ny)
+    g = rng(seed)
+    cx = {a: np.cos(2 * np.pi * a * xc / w.lx) for a, _, _ in modes}
+    cy = {b: np.cos(2 * np.pi * b * yc / w.ly) for _, b, _ in modes}
+    slab = max(1, (1 << 26) // (nx * ny))
+    for k0 in range(0, nz, slab):
+        k1 = min(nz, k0 + slab)
+        blk = out[k0:k1]
+        if noise_sigma:
+            blk[:] = g.standard_normal(blk.shape)
+            if noise_sigma != 1.0:
+                blk *= noise_sigma
+        else:
+            blk[:] = 0.0
+        for a, b, m in modes:
+            cz = np.cos(np.pi * m * zc[k0:k1])
+            blk += cz[:, None, None] * np.outer(cy[b], cx[a])[None]
+    return out, modes

@@ -1,0 +1,212 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py times.
+
+* Poisson solve at 512 x 512 x 384: 16 sampled (kx, ky) columns of the GPU
+  solution against the sampled-mode oracle (direct FP64 DFT of the rhs and the
+  oracle's own column solves), within 1e-12; FP64 residual of the whole field.
+* One RK3 substep at 512 x 512 x 384 (Rayleigh-Benard) and at 1024 x 512 x 256
+  (plane Couette, no scalar) element by element against the full FP64 oracle,
+  within 1e-12 (the oracle takes about 10-20 s on the host cores here).
+* Size-independent properties: max |div| after the pressure correction and
+  after a substep (the paper's O(1e-13), Sec. 2.2), the exactly steady
+  conduction state at full size.
+* Mixed precision at full size within 1e-10 of the (pinned) FP64 solve.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import sampled, timestep as ts
+from tests.helpers import cpu, gpu, make_ctx, ogrid, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+EPS = 2.220446049250313e-16
+
+
+def div_roundoff_scale(g, fields):
+    """Size of one rounding error of the divergence stencil:
+    max|u, v, w| (1/dx + 1/dy + 1/min dzc). The paper's O(1e-13) residual
+    divergence (Sec. 2.2) is this scale times a few units of round-off; at
+    512 x 512 x 384 with O(1) velocities the scale itself is about 1e-12."""
+    vmax = max(float(f.abs().max()) for f in fields)
+    return vmax * (1.0 / g.dx + 1.0 / g.dy + 1.0 / float(g.dzc.min()))
+
+
+def residual_fp64(ctx, g, b, phi):
+    """||b - mean_W(b) - L phi|| / ||b - mean_W(b)|| on the device (test-side check)."""
+    dzc = torch.as_tensor(g.dzc.numpy(), device=b.device)[:, None, None]
+    mb = (dzc * b).sum() / (dzc.sum() * g.nx * g.ny)
+    rdx2, rdy2 = 1.0 / g.dx**2, 1.0 / g.dy**2
+    L = (torch.roll(phi, 1, 2) - 2 * phi + torch.roll(phi, -1, 2)) * rdx2 \
+        + (torch.roll(phi, 1, 1) - 2 * phi + torch.roll(phi, -1, 1)) * rdy2
+    dzf = torch.as_tensor(g.dzf.numpy(), device=b.device)[:, None, None]
+    flux = torch.zeros((g.nz + 1, g.ny, g.nx), dtype=torch.float64, device=b.device)
+    flux[1:-1] = (phi[1:] - phi[:-1]) / dzf[1:-1]
+    L = L + (flux[1:] - flux[:-1]) / dzc
+    r = (b - mb) - L
+    return float(r.norm() / (b - mb).norm())
+
+
+def test_rb512_poisson_sampled_modes():
+    w = synth.workload("rb512")
+    g = ogrid(w)
+    b = synth.noise(g.cell_shape(), seed=123) + 0.01
+    ctx = make_ctx(w)
+    B = gpu(b)
+    phi = ctx.poisson_solve(B)
+    assert residual_fp64(ctx, g, B, phi) < 1e-13
+    pairs = sampled.default_pairs(g, seed=1, count=16)
+    ref = sampled.solve_modes(g, b, pairs)
+    got = sampled.mode_columns(g, phi, pairs)
+    num = sum(np.linalg.norm(got[p] - ref[p]) ** 2 for p in pairs)
+    den = sum(np.linalg.norm(ref[p]) ** 2 for p in pairs)
+    assert np.sqrt(num / den) < 1e-12
+    for p in pairs:   # every sampled column on its own
+        assert np.linalg.norm(got[p] - ref[p]) <= 1e-11 * np.linalg.norm(ref[p]) + 1e-14 * np.sqrt(den)
+
+
+def test_rb512_pressure_correction_divergence():
+    w = synth.workload("rb512")
+    u, v, ww = synth.velocity_noise(w, seed=7)
+    ctx = make_ctx(w)
+    X = [gpu(a) for a in (u, v, ww, np.zeros((w.nz, w.ny, w.nx)))]
+    info = ctx.project(*X, 1.0, 0.0, info=True)
+    g = ogrid(w)
+    bound = 8 * EPS * div_roundoff_scale(g, X[:3])
+    assert info["max_div"] < bound, (info["max_div"], bound)
+    dzc = torch.as_tensor(g.dzc.numpy(), device="cuda")[:, None, None]
+    d = (torch.roll(X[0], -1, 2) - X[0]) / g.dx + (torch.roll(X[1], -1, 1) - X[1]) / g.dy \
+        + (X[2][1:] - X[2][:-1]) / dzc
+    assert float(d.abs().max()) < bound
+
+
+def perturbed_rb(w, seed):
+    u, v, ww, T, p = synth.rb_initial(w, seed)
+    un, vn, wn = synth.velocity_noise(w, seed + 1, sigma=0.05)
+    return [u + un, v + vn, ww + wn, T, p]
+
+
+def substep_parity(w, state, ph, l, dt, has_T=True):
+    g = ogrid(w)
+    ctx = make_ctx(w)
+    S = [gpu(a) if a is not None else None for a in state]
+    H = [torch.zeros_like(S[0]), torch.zeros_like(S[1]), torch.zeros_like(S[2]),
+         torch.zeros_like(S[3]) if has_T else None]
+    ctx.rk3_substep(l, dt, *S, *H)
+    torch.cuda.synchronize()
+    ref, Href = ts.substep(g, ph, l, dt, tuple(cpu(a) if a is not None else None for a in state), None)
+    for n, a, b in zip("uvwTp", S, ref):
+        if b is None:
+            continue
+        assert rel_l2(a, b) < 1e-12, n
+    for a, b in zip(H, Href):
+        if b is not None:
+            assert rel_l2(a, b) < 1e-12
+    # residual divergence: no larger than what the FP64 oracle itself leaves
+    from oracle import operators as op
+    md = float(ctx.max_divergence(S[0], S[1], S[2]))
+    md_ref = float(op.divergence(g, ref[0], ref[1], ref[2]).abs().max())
+    assert md <= max(4 * md_ref, 8 * EPS * div_roundoff_scale(g, S[:3])), (md, md_ref)
+
+
+def test_rb512_substep_vs_oracle():
+    w = synth.workload("rb512")
+    ph = ts.Phys(nu=w.nu, kappa=w.kappa, buoyancy=1.0, T_bot=1.0, T_top=0.0)
+    substep_parity(w, perturbed_rb(w, 0), ph, 0, 2e-3)
+
+
+def test_couette1024_substep_vs_oracle():
+    w = synth.workload("couette1024")
+    u, v, ww, p = synth.couette_initial(w, seed=0)
+    ph = ts.Phys(nu=w.nu, u_bot=-1.0, u_top=1.0)
+    substep_parity(w, [u, v, ww, None, p], ph, 0, 5e-3, has_T=False)
+
+
+def test_rb512_conduction_steady_fullsize():
+    """The conduction profile is an exact steady state at any size (pinned in the
+    oracle): after a full step at 512 x 512 x 384 velocity stays at round-off and
+    T does not move."""
+    w = synth.workload("rb512")
+    u, v, ww, T, p = synth.rb_initial(w, 0, amp=0.0)
+    ctx = make_ctx(w)
+    S = [gpu(a) for a in (u, v, ww, T, p)]
+    T0 = S[3].clone()
+    H = [torch.zeros_like(S[0]), torch.zeros_like(S[1]), torch.zeros_like(S[2]), torch.zeros_like(S[3])]
+    ctx.cfl(S[0], S[1], S[2], w.cfl, w.dt_max)
+    for l in range(3):
+        ctx.rk3_substep(l, -1.0, *S, *H)
+    assert max(float(S[i].abs().max()) for i in range(3)) < 1e-13
+    assert float((S[3] - T0).abs().max()) < 1e-13
+
+
+def test_rb512_mixed_vs_fp64():
+    w = synth.workload("rb512")
+    g = ogrid(w)
+    b = gpu(synth.noise(g.cell_shape(), seed=5))
+    ctx64 = make_ctx(w, poisson_only=True)
+    ref = ctx64.poisson_solve(b)
+    del ctx64
+    ctxm = make_ctx(w, precision="mixed", refine_tol=1e-12, refine_max_iter=6, poisson_only=True)
+    phi, info = ctxm.poisson_solve(b, info=True)
+    assert info["status"] in (0, 5)
+    assert rel_l2(phi, ref) < 1e-10, info
+
+
+def test_poisson2048_mixed_sampled_and_closed_form():
+    """Large mixed-precision solve, 2048 x 2048 x 1024, tanh-stretched z: rhs =
+    N(0,1) noise + 8 manufactured modes. 16 sampled (kx, ky) columns (the 8
+    manufactured pairs among them) against the sampled-mode FP64 oracle within
+    1e-10; the modes-only solve against the continuum closed form
+    -sum cos cos cos / (4 pi^2 a^2 + 4 pi^2 b^2 + pi^2 m^2) (second-order
+    discretisation error, reported)."""
+    import math
+    free, total = torch.cuda.mem_get_info()
+    if free < 230e9:
+        pytest.skip("needs about 230 GB of free device memory")
+    w = synth.workload("poisson2048")
+    g = ogrid(w)
+    b, modes = synth.manufactured_rhs(w, seed=0)
+    pairs = [(a, bb) for a, bb, _ in modes]
+    for p in sampled.default_pairs(g, seed=2, count=10):
+        if p not in pairs:
+            pairs.append(p)
+    ref = sampled.solve_modes(g, b, pairs)
+    ctx = make_ctx(w, precision="mixed", refine_tol=1e-12, refine_max_iter=6, poisson_only=True)
+    B = torch.from_numpy(b).cuda()
+    phi, info = ctx.poisson_solve(B, info=True)
+    assert info["status"] in (0, 5), info
+    got = sampled.mode_columns(g, phi, pairs)
+    num = sum(np.linalg.norm(got[p] - ref[p]) ** 2 for p in pairs)
+    den = sum(np.linalg.norm(ref[p]) ** 2 for p in pairs)
+    err_sampled = math.sqrt(num / den)
+    assert err_sampled < 1e-10, (err_sampled, info)
+    # modes only, against the continuum closed form
+    synth.manufactured_rhs(w, seed=0, noise_sigma=0.0, modes=modes, out=b)
+    B.copy_(torch.from_numpy(b))
+    del b
+    ctx.poisson_solve(B, phi)
+    dev = phi.device
+    zc = torch.as_tensor(g.zc.numpy(), device=dev)
+    xc = (torch.arange(w.nx, device=dev, dtype=torch.float64) + 0.5) / w.nx
+    yc = (torch.arange(w.ny, device=dev, dtype=torch.float64) + 0.5) / w.ny
+    exact = B    # reuse the device buffer for the closed form
+    exact.zero_()
+    for a, bb, m in modes:
+        lam = 4 * math.pi**2 * (a**2 + bb**2) + math.pi**2 * m**2
+        exact -= (torch.cos(math.pi * m * zc)[:, None, None] * torch.cos(2 * math.pi * bb * yc)[None, :, None]
+                  * torch.cos(2 * math.pi * a * xc)[None, None, :]) / lam
+    dzc = torch.as_tensor(g.dzc.numpy(), device=dev)[:, None, None]
+    wmean = lambda f: float((dzc * f).sum() / (dzc.sum() * w.nx * w.ny))
+    exact -= wmean(exact)
+    err_closed = float((phi - exact).norm() / exact.norm())
+    print("poisson2048: sampled-mode error %.3e, closed-form error %.3e, iterations %d"
+          % (err_sampled, err_closed, info["iters"]))
+    assert err_closed < 1e-3

@@ -196,3 +196,21 @@ def test_mean_removal_and_gauge():
     assert abs(float(poisson.weighted_mean(g, phi))) < 1e-15
     r = op.laplacian(g, phi) - (b - mb)
     assert float(r.abs().max()) < 1e-11 * float(b.abs().max())
+
+
+def test_sampled_mode_oracle_matches_full_solve():
+    """The sampled-mode oracle (direct DFT + the same column solves) against the
+    FFT of the full oracle solve, and its direct DFT against the library FFT."""
+    from oracle import sampled
+    g = grid(32, 16, 11, stretch=1.5, lx=1.3, ly=0.7)
+    b = t(synth.noise(g.cell_shape(), seed=4)) + 0.2
+    pairs = sampled.default_pairs(g, count=12)
+    bh = torch.fft.rfft2(b).numpy()
+    cols = sampled.mode_columns(g, b, pairs)
+    for (kx, ky), v in cols.items():
+        np.testing.assert_allclose(v, bh[:, ky, kx], atol=1e-12 * np.abs(bh).max())
+    ph = torch.fft.rfft2(poisson.solve(g, b)).numpy()
+    got = sampled.solve_modes(g, b, pairs)
+    scale = np.abs(ph).max()
+    for (kx, ky), v in got.items():
+        np.testing.assert_allclose(v, ph[:, ky, kx], atol=1e-12 * scale)
