@@ -155,7 +155,7 @@ def family_work(fam: str, w):
       fft_y  fft_ops(ny) per complex point (nx/2+1 complex per row)
       thomas 7 per complex point (4 forward, 3 backward)
       project 12; rhs 120 (u 31, v 28, w 35, T 27); crank_nicolson 16 (4 fields);
-      cfl_reduce 9."""
+      cfl_reduce 7 (|.| is an operand modifier)."""
     nx, ny, nz = w.nx, w.ny, w.nz
     n = nx * ny * nz
     M1 = nx // 2 + 1
@@ -175,7 +175,7 @@ def family_work(fam: str, w):
     if fam == "crank_nicolson":
         return 4 * 24 * n, 16 * n
     if fam == "cfl_reduce":
-        return 24 * n, 9 * n
+        return 24 * n, 7 * n
     return None
 
 
