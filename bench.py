@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--poisson-only", action="store_true",
                     help="only the Poisson-solve side measurement (FP64 and mixed)")
+    ap.add_argument("--no-tma", action="store_true",
+                    help="use the plain y-transform kernel instead of the TMA-staged one")
     ap.add_argument("--grid", default=None,
                     help="override the workload's cells as NXxNYxNZ (profiling smaller cases)")
     return ap.parse_args()
@@ -243,7 +245,8 @@ def run_poisson_only(args):
     else:
         b = torch.as_tensor(synth.noise((w.nz, w.ny, w.nx), seed=123)).to(dev)
     out = {}
-    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), poisson_only=True)
+    tma = not args.no_tma
+    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), poisson_only=True, tma=tma)
     phi64 = torch.empty_like(b)
     ms64 = timed(lambda: ctx.poisson_solve(b, phi64), 5, stream)
     ctx.profile(True)
@@ -255,7 +258,7 @@ def run_poisson_only(args):
     torch.cuda.synchronize()
     out["poisson_fp64"] = {"ms": ms64, "grid_points_per_s": pts / (ms64 / 1e3), "families_ms": fam64}
     mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=1e-12,
-                   refine_max_iter=6, poisson_only=True)
+                   refine_max_iter=6, poisson_only=True, tma=tma)
     phim = torch.empty_like(b)
     _, info = mctx.poisson_solve(b, phim, info=True)
     msm = timed(lambda: mctx.poisson_solve(b, phim), 5, stream)
@@ -267,7 +270,7 @@ def run_poisson_only(args):
     out["poisson_mixed"] = {"ms": msm, "grid_points_per_s": pts / (msm / 1e3), "iters": info["iters"],
                             "rel_l2_vs_fp64_gpu": err, "err_estimate": info["err_estimate"],
                             "speedup_vs_fp64": ms64 / msm, "families_ms": famm}
-    print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "poisson": out}))
+    print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "tma_y": tma, "poisson": out}))
 
 
 def run_ours(args):
@@ -289,7 +292,7 @@ def run_ours(args):
     w = workload_from(args)
     ph = Physics(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, u_bot=w.u_bot, u_top=w.u_top,
                  T_bot=w.T_bot, T_top=w.T_top)
-    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), phys=ph)
+    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), phys=ph, tma=not args.no_tma)
     if w.has_T:
         host = synth.rb_initial(w, seed=rank)
     else:
@@ -411,7 +414,7 @@ def run_ours(args):
     # ---- side measurements: Poisson solve alone, FP64 vs mixed
     extra = {}
     if not args.no_extra and rank == 0:
-        extra = side_measurements(ctx, w, dev)
+        extra = side_measurements(ctx, w, dev, tma=not args.no_tma)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -456,7 +459,7 @@ def timed(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def side_measurements(ctx, w, dev):
+def side_measurements(ctx, w, dev, tma=True):
     """Poisson solve alone on the same grid: FP64 direct vs mixed FP32 + FP64
     refinement, with the mixed error against the FP64 GPU solve."""
     import torch
@@ -470,7 +473,7 @@ def side_measurements(ctx, w, dev):
     out = {"poisson_fp64": {"ms": ms64, "grid_points_per_s": pts / (ms64 / 1e3)}}
     try:
         mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=1e-12,
-                       refine_max_iter=6, poisson_only=True)
+                       refine_max_iter=6, poisson_only=True, tma=tma)
         phim = torch.empty_like(b)
         _, info = mctx.poisson_solve(b, phim, info=True)
         msm = timed(lambda: mctx.poisson_solve(b, phim), 5, stream)
@@ -490,7 +493,33 @@ def side_measurements(ctx, w, dev):
     ctx.poisson_solve(b, phi64)
     out["poisson_fp64"]["families_ms"] = {k: v[0] for k, v in ctx.profile_read().items() if v[1]}
     ctx.profile(False)
+    out["cufft_comparison"] = cufft_comparison(b, out, stream)
     return out
+
+
+def cufft_comparison(b, out, stream):
+    """Timing comparison only (never on the product path): the library's batched
+    2-D real FFT pair (forward rfft2 + inverse irfft2 over the z planes, through
+    torch.fft) next to this build's transform kernels inside one solve (the x
+    transforms with their fused divergence/scaling plus the two y passes)."""
+    import torch
+    res = {}
+    fams64 = out["poisson_fp64"].get("families_ms", {})
+    ours64 = sum(fams64.get(k, 0.0) for k in ("r2c_x", "fft_y", "c2r_x"))
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        x = b.to(dt)
+        ms = timed(lambda: torch.fft.irfft2(torch.fft.rfft2(x), s=x.shape[-2:]), 5, stream)
+        res[name] = {"library_rfft2_irfft2_ms": ms}
+        del x
+    res["fp64"]["this_build_fft_passes_ms"] = ours64
+    res["fp64"]["ratio_library_over_this_build"] = res["fp64"]["library_rfft2_irfft2_ms"] / max(ours64, 1e-9)
+    fm = out.get("poisson_mixed", {}).get("families_ms")
+    if fm:
+        it = max(out["poisson_mixed"].get("iters", 1), 1)
+        ours32 = sum(fm.get(k, 0.0) for k in ("r2c_x", "fft_y", "c2r_x")) / it
+        res["fp32"]["this_build_fft_passes_ms_per_iteration"] = ours32
+        res["fp32"]["ratio_library_over_this_build"] = res["fp32"]["library_rfft2_irfft2_ms"] / max(ours32, 1e-9)
+    return res
 
 
 # ------------------------------------------------------------------ reference arm

@@ -46,7 +46,11 @@ typedef enum {
   AFID_ERR_INCONSISTENT_RHS = 5, /* |weighted mean of rhs| > 1e-8 max|rhs| (reported only
                                     when afid_info is requested; the mean is removed)     */
   AFID_ERR_CUDA = 6,             /* a CUDA runtime call failed                            */
-  AFID_ERR_OOM = 7               /* workspace allocation failed in afid_create            */
+  AFID_ERR_OOM = 7,              /* workspace allocation failed in afid_create            */
+  AFID_ERR_TIMEOUT = 8           /* a bounded wait inside a kernel (TMA tile copy) gave
+                                    up; reported by the next call that fills afid_info;
+                                    the results of the calls since the last check are
+                                    not valid                                             */
 } afid_status;
 
 typedef enum {
@@ -61,6 +65,9 @@ typedef enum {
                                solver (chunked Thomas per lane + parallel cyclic reduction
                                across the warp) instead of one system per thread -- the
                                variant for long wall-normal columns and few modes */
+#define AFID_NO_TMA 4       /* mixed: use the plain y-transform kernel (per-block loads into
+                               padded shared memory) instead of the TMA-staged persistent
+                               one for the FP32 passes (FP64 always uses the plain one) */
 
 typedef struct {
   int nx, ny, nz;          /* cells; nx, ny powers of two                            */
@@ -70,7 +77,7 @@ typedef struct {
   double refine_tol;       /* mixed: stop when the estimated relative error of phi
                               is <= refine_tol (see afid_info.err_estimate)          */
   int refine_max_iter;     /* mixed: maximum refinement iterations (>= 1)             */
-  int flags;               /* AFID_POISSON_ONLY or 0                                 */
+  int flags;               /* OR of the AFID_* flags above, or 0                     */
 } afid_grid_desc;
 
 typedef struct {

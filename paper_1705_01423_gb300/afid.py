@@ -28,10 +28,12 @@ AFID_ERR_NOT_CONVERGED = 4
 AFID_ERR_INCONSISTENT_RHS = 5
 AFID_ERR_CUDA = 6
 AFID_ERR_OOM = 7
+AFID_ERR_TIMEOUT = 8
 AFID_FP64 = 0
 AFID_MIXED = 1
 AFID_POISSON_ONLY = 1
 AFID_WARP_TRIDIAG = 2
+AFID_NO_TMA = 4
 
 
 class GridDesc(C.Structure):
@@ -150,7 +152,7 @@ class Context:
 
     def __init__(self, nx, ny, nz, lx, ly, zf, precision="fp64", refine_tol=1e-12,
                  refine_max_iter=10, phys: Physics | None = None, poisson_only=False,
-                 warp_tridiag=False, stream=None):
+                 warp_tridiag=False, tma=True, stream=None):
         import torch
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.lx, self.ly = float(lx), float(ly)
@@ -163,7 +165,8 @@ class Context:
                         self._zf.ctypes.data_as(C.POINTER(C.c_double)),
                         AFID_MIXED if precision == "mixed" else AFID_FP64, float(refine_tol),
                         int(refine_max_iter),
-                        (AFID_POISSON_ONLY if poisson_only else 0) | (AFID_WARP_TRIDIAG if warp_tridiag else 0))
+                        (AFID_POISSON_ONLY if poisson_only else 0) | (AFID_WARP_TRIDIAG if warp_tridiag else 0)
+                        | (0 if tma else AFID_NO_TMA))
         self._desc = desc
         ph = PhysDesc(self.phys.nu, self.phys.kappa, self.phys.buoyancy, self.phys.u_bot,
                       self.phys.u_top, self.phys.T_bot, self.phys.T_top)

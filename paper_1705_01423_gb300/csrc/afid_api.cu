@@ -101,6 +101,10 @@ afid_status fill_info(afid_ctx* c, afid_info* info, bool mixed, bool want_div) {
   double s[S_COUNT];
   if (cudaMemcpy(s, c->scal, sizeof(s), cudaMemcpyDeviceToHost) != cudaSuccess) return AFID_ERR_CUDA;
   std::memset(info, 0, sizeof(*info));
+  if (s[S_FAULT] != 0.0) {
+    cudaMemsetAsync(c->scal + S_FAULT, 0, sizeof(double), c->stream);
+    return AFID_ERR_TIMEOUT;
+  }
   double amax;
   std::memcpy(&amax, &s[S_RHS_ABSMAX], sizeof(double));
   info->rhs_absmax = amax;
@@ -162,6 +166,7 @@ const char* afid_status_string(afid_status s) {
     case AFID_ERR_INCONSISTENT_RHS: return "right-hand side has a non-zero weighted mean (removed)";
     case AFID_ERR_CUDA: return "CUDA runtime error";
     case AFID_ERR_OOM: return "device out of memory";
+    case AFID_ERR_TIMEOUT: return "a bounded wait inside a kernel timed out (results not valid)";
   }
   return "unknown status";
 }
@@ -362,6 +367,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   ok = ok && cudaMemset(c->scal, 0, S_COUNT * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMemset(c->cntab, 0, (size_t)3 * 4 * (nz + 1) * sizeof(double)) == cudaSuccess;
   ok = ok && init_thomas_tables(c) == cudaSuccess;
+  ok = ok && ((c->flags & AFID_NO_TMA) || init_ffty_tma(c) == cudaSuccess);
   ok = ok && cudaStreamSynchronize(c->stream) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();

@@ -1,5 +1,6 @@
 // Internal definitions shared by the libafid translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <vector>
@@ -43,6 +44,7 @@ enum Scalar {
   S_ERREST,        // mixed: estimated relative error of phi
   S_D1NORM2,       // mixed: ||d_1||^2 (the first correction, a proxy for ||phi||^2)
   S_PHIMEAN,       // mixed: weighted mean of phi after the last correction
+  S_FAULT,         // 1.0 when a bounded wait inside a kernel gave up
   S_COUNT = 20
 };
 
@@ -132,12 +134,23 @@ struct afid_ctx {
   size_t bytes;
   long long launches;
   afid::Prof* prof;
+  // TMA-staged FP32 y transforms: tensor map of the spectral workspace and
+  // launch shape; tma_y = 0 when unused (FP64 contexts, ny > 512, AFID_NO_TMA)
+  CUtensorMap tmy;
+  int tma_y;
+  int tmy_stages, tmy_threads, tmy_blocks_per_sm;
+  size_t tmy_smem;
 };
 
 namespace afid {
 
 // launchers (stream-ordered; return cudaError_t of the launch)
 cudaError_t init_thomas_tables(afid_ctx* c);
+// TMA y transform of the FP32 (mixed-precision) spectral passes: set-up at
+// create, launch
+cudaError_t init_ffty_tma(afid_ctx* c);
+template <typename R>
+cudaError_t run_fft_y_tma(afid_ctx* c, const typename cplx<R>::T* tw, bool inv, const double* skip);
 // Direct FP64 solve of L phi = src / s, src = rhs (rhs != NULL) or D(u, v, w);
 // s is read from the device scalar S_PROJ_S when `dev_s`, else 1.
 cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, const double* v,

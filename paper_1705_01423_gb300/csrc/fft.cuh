@@ -81,14 +81,25 @@ template <bool INV, typename C> __device__ __forceinline__ void dft8(C* a) {
   a[7] = csub(e3, o3);
 }
 
-// One Stockham pass of radix R on a padded shared-memory line `buf` of N points,
-// span p (size of the sub-transforms already done). `t` in [0, N/8) is the
-// thread's index within the line. All reads happen before the barrier, all
-// writes after it, so the pass is in place. The caller guarantees that every
-// thread of the block calls this (barriers inside).
-template <int R, bool INV, typename C>
-__device__ __forceinline__ void stockham_pass(C* buf, int N, int p, const C* tw, int twstride,
-                                              int t, bool active) {
+// Shared-memory slot of point m of a line: padded line (one slot every 8
+// points), or column c of a tile of TK interleaved lines (point m of every
+// line in one row of TK slots, as a TMA box lands in shared memory).
+struct PadIx {
+  __device__ __forceinline__ int operator()(int m) const { return pad8(m); }
+};
+template <int TK> struct ColIx {
+  int c;
+  __device__ __forceinline__ int operator()(int m) const { return m * TK + c; }
+};
+
+// One Stockham pass of radix R on a shared-memory line `buf` of N points
+// (slot of point m: ix(m)), span p (size of the sub-transforms already done).
+// `t` in [0, N/8) is the thread's index within the line. All reads happen
+// before the barrier, all writes after it, so the pass is in place. The
+// caller guarantees that every thread of the block calls this (barriers inside).
+template <int R, bool INV, typename C, typename IX>
+__device__ __forceinline__ void stockham_pass_ix(C* buf, int N, int p, const C* tw, int twstride,
+                                                 int t, bool active, IX ix) {
   constexpr int B = 8 / R;  // butterflies per thread
   C x[8];
   const int nb = N / R;
@@ -97,7 +108,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, int N, int p, const C* tw,
     for (int b = 0; b < B; ++b) {
       const int j = t + b * (N / 8);
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[b * R + r] = buf[pad8(j + r * nb)];
+      for (int r = 0; r < R; ++r) x[b * R + r] = buf[ix(j + r * nb)];
     }
   }
   __syncthreads();
@@ -120,22 +131,34 @@ __device__ __forceinline__ void stockham_pass(C* buf, int N, int p, const C* tw,
       if (R == 2) dft2<INV>(y[0], y[1]);
       const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[pad8(o + r * p)] = y[r];
+      for (int r = 0; r < R; ++r) buf[ix(o + r * p)] = y[r];
     }
   }
   __syncthreads();
 }
 
-// Full N-point transform of one padded line; N = 2^n, 8 <= N.
-template <bool INV, typename C>
-__device__ __forceinline__ void fft_line(C* buf, int N, const C* tw, int twstride, int t, bool active) {
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void stockham_pass(C* buf, int N, int p, const C* tw, int twstride,
+                                              int t, bool active) {
+  stockham_pass_ix<R, INV>(buf, N, p, tw, twstride, t, active, PadIx{});
+}
+
+// Full N-point transform of one line; N = 2^n, 8 <= N.
+template <bool INV, typename C, typename IX>
+__device__ __forceinline__ void fft_line_ix(C* buf, int N, const C* tw, int twstride, int t,
+                                            bool active, IX ix) {
   int p = 1;
   while (N / p >= 8) {
-    stockham_pass<8, INV>(buf, N, p, tw, twstride, t, active);
+    stockham_pass_ix<8, INV>(buf, N, p, tw, twstride, t, active, ix);
     p *= 8;
   }
-  if (N / p == 4) stockham_pass<4, INV>(buf, N, p, tw, twstride, t, active);
-  else if (N / p == 2) stockham_pass<2, INV>(buf, N, p, tw, twstride, t, active);
+  if (N / p == 4) stockham_pass_ix<4, INV>(buf, N, p, tw, twstride, t, active, ix);
+  else if (N / p == 2) stockham_pass_ix<2, INV>(buf, N, p, tw, twstride, t, active, ix);
+}
+
+template <bool INV, typename C>
+__device__ __forceinline__ void fft_line(C* buf, int N, const C* tw, int twstride, int t, bool active) {
+  fft_line_ix<INV>(buf, N, tw, twstride, t, active, PadIx{});
 }
 
 }  // namespace afid

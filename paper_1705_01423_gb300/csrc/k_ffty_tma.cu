@@ -1,0 +1,211 @@
+// Complex FFT along y (Sec. 2.2, the second of the two periodic transforms)
+// with TMA-staged tiles: the on-device replacement of the paper's y-pencil
+// transpose (Sec. 3.5).
+//
+// The spectral array [nz][ny][P] (complex, row pitch P) is read as a 3-D
+// tensor of scalars {2 (M + 1), ny, nz}. One tile is TK consecutive kx
+// columns x all ny rows of one z plane; its box lands in shared memory as
+// rows of TK complex values (TK x element = 128 bytes), so that the TK lines
+// are transformed side by side: the lanes of a warp run along kx and every
+// Stockham access reads or writes whole 128-byte rows (no bank conflicts, no
+// padding). Columns beyond kx = M are outside the tensor: they load as zeros
+// and are not stored.
+//
+// A persistent block walks its tiles with a ring of S shared-memory stages:
+// while tile i is transformed, the load of tile i+1 and the store of tile i-1
+// are in flight (one mbarrier per stage for loads, bulk groups for stores).
+// Waits are bounded; a timeout sets the device flag S_FAULT and the block
+// stops after waiting (again bounded) for its own copies in flight.
+#include "afid_internal.cuh"
+#include "fft.cuh"
+#include "tma.cuh"
+
+namespace afid {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+
+// Used for the FP32 transforms of the mixed-precision solve, which are bound
+// by HBM bandwidth. The FP64 transforms stay on the plain kernel: they are
+// bound by the FP64 issue rate, and there two 512-thread blocks per SM of the
+// plain kernel keep the FP64 pipe busier than one block of this ring (whose
+// 64 KB stages allow one block per SM at ny = 512); measured at 512 x 512 x
+// 384, 5.08 ms (plain) against 5.46 ms (ring) for the two y passes of a solve.
+template <typename R>
+struct TileK;
+// TK columns per tile (TK x complex = 128-byte rows); MAXT = TK x 512/8, the
+// block size at the largest ny served (512)
+template <> struct TileK<float> { static constexpr int TK = 16, MAXT = 1024; };
+
+template <typename R, bool INV>
+__global__ void __launch_bounds__(TileK<R>::MAXT, 1) k_fft_y_tma(const __grid_constant__ CUtensorMap map, Grid g,
+                                                       const typename cplx<R>::T* __restrict__ tw,
+                                                       const double* __restrict__ skip,
+                                                       double* __restrict__ scal, int stages,
+                                                       int ntile_x) {
+  using C = typename cplx<R>::T;
+  constexpr int TK = TileK<R>::TK;
+  if (skip && *skip != 0.0) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int N = g.ny;
+  const int tile_elems = TK * N;
+  C* tiles = reinterpret_cast<C*>(smem_raw);
+  C* stw = tiles + (size_t)stages * tile_elems;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stw + N);
+  const int tid = threadIdx.x;
+  const int BR = N < 256 ? N : 256;  // rows per box (box extents are <= 256)
+  const uint32_t tile_bytes = (uint32_t)(tile_elems * sizeof(C));
+  const int ntiles = ntile_x * g.nz;
+  const int first = blockIdx.x;
+  const int count = first < ntiles ? (ntiles - 1 - first) / gridDim.x + 1 : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(&bar[s], 1);
+    fence_barrier_init();
+  }
+  for (int q = tid; q < N; q += blockDim.x) stw[q] = tw[q];
+  __syncthreads();
+
+  // thread 0: start the loads of local tile `it` into stage it % stages
+  auto issue = [&](int it) {
+    const int tile = first + it * gridDim.x;
+    const int s = it % stages;
+    const int kxt = tile % ntile_x, z = tile / ntile_x;
+    mbar_expect_tx(&bar[s], tile_bytes);
+    for (int y0 = 0; y0 < N; y0 += BR)
+      tma_load_3d(tiles + (size_t)s * tile_elems + (size_t)y0 * TK, &map, &bar[s], 2 * kxt * TK, y0, z);
+  };
+  if (tid == 0 && count > 0) issue(0);
+
+  const int c = tid % TK, t = tid / TK;  // column within the tile, thread within the line
+  bool failed = false;
+  int it = 0;
+  for (; it < count; ++it) {
+    const int s = it % stages;
+    if (tid == 0 && it + 1 < count) {
+      // stage (it+1) % stages last held tile it+1-stages: its store must have
+      // finished reading shared memory before the next load overwrites it
+      if (stages >= 3) bulk_wait_read<1>();
+      else bulk_wait_read<0>();
+      issue(it + 1);
+    }
+    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it / stages) & 1), kWaitLimitNs);
+    if (__syncthreads_or(!ok)) {  // block-uniform decision
+      failed = true;
+      break;
+    }
+    C* buf = tiles + (size_t)s * tile_elems;
+    fft_line_ix<INV>(buf, N, stw, 1, t, true, ColIx<TK>{c});
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      const int tile = first + it * gridDim.x;
+      const int kxt = tile % ntile_x, z = tile / ntile_x;
+      for (int y0 = 0; y0 < N; y0 += BR) tma_store_3d(&map, buf + (size_t)y0 * TK, 2 * kxt * TK, y0, z);
+      bulk_commit();
+    }
+  }
+  if (tid == 0) {
+    if (failed) {
+      scal[S_FAULT] = 1.0;
+      // loads of tiles it and it+1 may still be in flight: wait for them (bounded)
+      for (int q = it; q < count && q <= it + 1; ++q)
+        mbar_wait_bounded(&bar[q % stages], (uint32_t)((q / stages) & 1), kWaitLimitNs);
+    }
+    bulk_wait<0>();  // every store complete before the block's shared memory is released
+  }
+}
+
+// Host: tensor map of the spectral workspace for the y transforms.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess && p)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+template <typename R>
+static size_t ffty_tma_smem(const Grid& g, int stages) {
+  using C = typename cplx<R>::T;
+  return (size_t)stages * TileK<R>::TK * g.ny * sizeof(C) + (size_t)g.ny * sizeof(C) + stages * sizeof(uint64_t);
+}
+
+// Sets up the TMA y transform of a mixed-precision context when the sizes
+// allow it (16 <= ny <= 512, a tile ring of at least two stages in shared
+// memory); leaves c->tma_y = 0 (the plain kernel is used) otherwise.
+cudaError_t init_ffty_tma(afid_ctx* c) {
+  c->tma_y = 0;
+  const Grid& g = c->g;
+  if (g.ny > 512 || g.ny < 8) return cudaSuccess;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaSuccess;
+  if (c->prec != AFID_MIXED) return cudaSuccess;
+  const int TK = TileK<float>::TK;
+  const size_t csz = sizeof(float2);
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  int stages = 3;
+  auto need = [&](int s) { return ffty_tma_smem<float>(g, s); };
+  // + static shared memory of the kernel (128 B)
+  while (stages > 2 && need(stages) + 256 > (size_t)smem_optin) --stages;
+  if (need(stages) + 256 > (size_t)smem_optin) return cudaSuccess;
+  const int threads = TK * (g.ny / 8);
+  if (threads > 1024 || threads < 32) return cudaSuccess;
+
+  cuuint64_t dims[3] = {(cuuint64_t)2 * (g.M + 1), (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  cuuint64_t strides[2] = {(cuuint64_t)g.P * csz, (cuuint64_t)g.ny * g.P * csz};
+  cuuint32_t box[3] = {(cuuint32_t)(2 * TK), (cuuint32_t)(g.ny < 256 ? g.ny : 256), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(&c->tmy, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                   c->spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaSuccess;
+  const size_t sm = need(stages);
+  cudaError_t e;
+  int per_sm = 0;
+  for (auto kf : {k_fft_y_tma<float, false>, k_fft_y_tma<float, true>})
+    if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_y_tma<float, false>, threads, sm);
+  if (e || per_sm < 1) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  c->tmy_stages = stages;
+  c->tmy_threads = threads;
+  c->tmy_smem = sm;
+  c->tmy_blocks_per_sm = per_sm;
+  c->tma_y = 1;
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t run_fft_y_tma(afid_ctx* c, const typename cplx<R>::T* tw, bool inv, const double* skip) {
+  const Grid& g = c->g;
+  constexpr int TK = TileK<R>::TK;
+  const int ntile_x = ceil_div(g.M + 1, TK);
+  const long long ntiles = (long long)ntile_x * g.nz;
+  long long blocks = (long long)c->num_sms * c->tmy_blocks_per_sm;
+  if (blocks > ntiles) blocks = ntiles;
+  auto kf = inv ? k_fft_y_tma<R, true> : k_fft_y_tma<R, false>;
+  kf<<<(int)blocks, c->tmy_threads, c->tmy_smem, c->stream>>>(c->tmy, g, tw, skip, c->scal, c->tmy_stages,
+                                                               ntile_x);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template cudaError_t run_fft_y_tma<float>(afid_ctx*, const float2*, bool, const double*);
+
+}  // namespace afid

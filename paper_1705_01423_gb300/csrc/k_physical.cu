@@ -209,17 +209,33 @@ __global__ void k_cn_tables(Grid g, Metric m, int l, double dt_in, double* __res
   double* cp = mm + L;
   double* sp = cp + L;
   const int k0 = o == 0 ? 0 : 1, k1 = g.nz;  // rows k0..nz-1
+  const double* __restrict__ pa = o == 0 ? m.ca : m.fa;
+  const double* __restrict__ pc = o == 0 ? m.cc : m.fc;
+  // The recurrence is serial; the coefficients of the next B rows are loaded
+  // together so that only the pivot chain is on the critical path.
+  constexpr int B = 8;
   double cprev = 0.0;
-  for (int k = k0; k < k1; ++k) {
-    const double a = o == 0 ? m.ca[k] : m.fa[k];
-    const double cc = o == 0 ? m.cc[k] : m.fc[k];
-    const double s = -beta * a, up = -beta * cc, d = 1.0 + beta * (a + cc);
-    const double mk = 1.0 / (d - (k == k0 ? 0.0 : s * cprev));
-    cprev = up * mk;
-    sub[k] = s;
-    mm[k] = mk;
-    cp[k] = cprev;
-    sp[k] = up;
+  for (int kb = k0; kb < k1; kb += B) {
+    double av[B], cv[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int k = kb + q < k1 ? kb + q : k1 - 1;
+      av[q] = pa[k];
+      cv[q] = pc[k];
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int k = kb + q;
+      if (k < k1) {
+        const double s = -beta * av[q], up = -beta * cv[q], d = 1.0 + beta * (av[q] + cv[q]);
+        const double mk = 1.0 / (d - (k == k0 ? 0.0 : s * cprev));
+        cprev = up * mk;
+        sub[k] = s;
+        mm[k] = mk;
+        cp[k] = cprev;
+        sp[k] = up;
+      }
+    }
   }
 }
 

@@ -594,39 +594,94 @@ __global__ void __launch_bounds__(128) k_tridiag_warp(Grid g, Metric m, CT* __re
 // dzc-weighted mean of bhat (solvability), flux prefix sums
 // F_{k+1} = F_k + dzc_k bhat_k, phi_k = phi_{k-1} + dzf_k F_k, then the gauge
 // (zero dzc-weighted mean). Also records the removed mean of the rhs.
-template <typename R>
-__global__ void k_zero_mode(Grid g, Metric m, typename cplx<R>::T* __restrict__ spec, double* scal,
-                            const double* __restrict__ skip) {
-  using C = typename cplx<R>::T;
-  if (skip && *skip != 0.0) return;
-  extern __shared__ double zb[];
-  const int nz = g.nz;
-  const size_t plane = (size_t)g.ny * g.P;
-  for (int k = threadIdx.x; k < nz; k += blockDim.x) zb[k] = (double)spec[k * plane].x;
+// Thread t owns the rows [t E, t E + E); the two recurrences are prefix sums,
+// taken as block-wide exclusive scans of the per-thread partial sums.
+
+// Exclusive prefix sum over the block of one double per thread, and the block
+// total. ws: 32 doubles of shared scratch; every thread of the block calls it.
+__device__ __forceinline__ double block_excl_scan(double v, double* ws, double* total) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  double ex = __shfl_up_sync(FULL, x, 1);
+  if (lane == 0) ex = 0.0;
+  if (lane == 31) ws[warp] = x;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double sw = 0.0, sb = 0.0;
-    for (int k = 0; k < nz; ++k) {
-      sw += m.dzc[k];
-      sb += m.dzc[k] * zb[k];
+  if (warp == 0) {
+    double s = lane < nw ? ws[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(FULL, s, o);
+      if (lane >= o) s += y;
     }
-    const double mu = sb / sw;
-    scal[S_RHS_MEAN] = mu / ((double)g.nx * (double)g.ny);
-    double F = 0.0, ph = 0.0, sp = 0.0;
-    double bprev = zb[0] - mu;
-    zb[0] = 0.0;
-    for (int k = 1; k < nz; ++k) {
-      F += m.dzc[k - 1] * bprev;
-      bprev = zb[k] - mu;
-      ph += m.dzf[k] * F;
-      zb[k] = ph;
-      sp += m.dzc[k] * ph;
-    }
-    const double pm = sp / sw;
-    for (int k = 0; k < nz; ++k) zb[k] -= pm;
+    ws[lane] = s;  // inclusive over the warps
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < nz; k += blockDim.x) spec[k * plane] = C{(R)zb[k], (R)0};
+  const double before = warp > 0 ? ws[warp - 1] + ex : ex;
+  *total = ws[nw - 1];
+  __syncthreads();  // ws free for the next call
+  return before;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_zero_mode(Grid g, Metric m, typename cplx<R>::T* __restrict__ spec,
+                                                    double* scal, const double* __restrict__ skip) {
+  using C = typename cplx<R>::T;
+  if (skip && *skip != 0.0) return;
+  extern __shared__ double zb[];  // nz values, then 32 doubles of scan scratch
+  double* ws = zb + g.nz;
+  const int nz = g.nz;
+  const size_t plane = (size_t)g.ny * g.P;
+  const int E = (nz + blockDim.x - 1) / blockDim.x;
+  const int k0 = min((int)threadIdx.x * E, nz), k1 = min(k0 + E, nz);
+  const double* __restrict__ dzc = m.dzc;
+  const double* __restrict__ dzf = m.dzf;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) zb[k] = (double)spec[k * plane].x;
+  __syncthreads();
+  double sw = 0.0, sb = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    sw += dzc[k];
+    sb += dzc[k] * zb[k];
+  }
+  double tsw, tsb, unused;
+  block_excl_scan(sw, ws, &tsw);
+  block_excl_scan(sb, ws, &tsb);
+  const double mu = tsb / tsw;
+  if (threadIdx.x == 0) scal[S_RHS_MEAN] = mu / ((double)g.nx * (double)g.ny);
+  // F at the first owned row: sum over all earlier rows of dzc (b - mu)
+  double f = 0.0;
+  for (int k = k0; k < k1; ++k) f += dzc[k] * (zb[k] - mu);
+  const double F0 = block_excl_scan(f, ws, &unused);
+  // phi at the row before the first owned one: sum of dzf_j F_j, 1 <= j < k0
+  double gs = 0.0, Fk = F0;
+  for (int k = k0; k < k1; ++k) {
+    if (k > 0) gs += dzf[k] * Fk;
+    Fk += dzc[k] * (zb[k] - mu);
+  }
+  double ph = block_excl_scan(gs, ws, &unused);
+  double sp = 0.0;
+  Fk = F0;
+  for (int k = k0; k < k1; ++k) {
+    if (k > 0) ph += dzf[k] * Fk;
+    Fk += dzc[k] * (zb[k] - mu);
+    zb[k] = ph;
+    sp += dzc[k] * ph;
+  }
+  double tsp;
+  block_excl_scan(sp, ws, &tsp);
+  const double pm = tsp / tsw;
+  for (int k = k0; k < k1; ++k) spec[k * plane] = C{(R)(zb[k] - pm), (R)0};
+}
+
+static void launch_zero_mode_threads(const Grid& g, int* thr, size_t* sm) {
+  int t = ((g.nz + 31) / 32) * 32;
+  *thr = t > 1024 ? 1024 : t;
+  *sm = (size_t)(g.nz + 32) * sizeof(double);
 }
 
 // --------------------------------------------------------------------------
@@ -647,6 +702,8 @@ template <typename R>
 static cudaError_t run_fft_y(afid_ctx* c, typename cplx<R>::T* spec, const typename cplx<R>::T* tw,
                              bool inv, const double* skip) {
   ProfScope ps(c, KF_FFTY);
+  if constexpr (sizeof(R) == sizeof(float))
+    if (c->tma_y) return run_fft_y_tma<float>(c, tw, inv, skip);
   const Grid& g = c->g;
   const size_t ls = line_smem<R>(g.ny);
   // widest tile that keeps a block within 1024 threads and ~112 KB of shared memory
@@ -742,7 +799,10 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
   }
   {
     ProfScope ps(c, KF_ZERO);
-    k_zero_mode<double><<<1, 256, g.nz * sizeof(double), c->stream>>>(g, c->m, spec, c->scal, nullptr);
+    int zt;
+    size_t zs;
+    launch_zero_mode_threads(g, &zt, &zs);
+    k_zero_mode<double><<<1, zt, zs, c->stream>>>(g, c->m, spec, c->scal, nullptr);
   }
   c->launches++;
   if ((e = cudaGetLastError())) return e;
@@ -779,7 +839,10 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, con
   }
   {
     ProfScope ps(c, KF_ZERO);
-    k_zero_mode<float><<<1, 256, g.nz * sizeof(double), c->stream>>>(g, c->m, spec, c->scal, skip);
+    int zt;
+    size_t zs;
+    launch_zero_mode_threads(g, &zt, &zs);
+    k_zero_mode<float><<<1, zt, zs, c->stream>>>(g, c->m, spec, c->scal, skip);
   }
   c->launches++;
   if ((e = cudaGetLastError())) return e;
