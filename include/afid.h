@@ -89,8 +89,9 @@ typedef struct {
 
 typedef struct {
   int iters;               /* refinement iterations used (1 for AFID_FP64)           */
-  double rel_residual;     /* mixed: ||r||_2/||b - mean||_2 of the residual computed
-                              before the last correction (the norms are only
+  double rel_residual;     /* mixed: ||r||_2/||b - mean||_2 of the FP64 residual
+                              computed before the last correction (||r||^2 summed
+                              from its FP32 rounding; the norms are only
                               accumulated when afid_info is requested); FP64: 0     */
   double rhs_mean;         /* cell-volume-weighted mean removed from the rhs         */
   double rhs_absmax;       /* max |rhs|                                              */

@@ -89,9 +89,9 @@ size_t spec_elems(const afid_grid_desc* d) {
 
 void free_all(afid_ctx* c) {
   void* ps[] = {c->metric_buf, c->twx64, c->twy64, c->twx32, c->twy32, c->mtab64, c->mtab32,
-                c->lamx, c->lamy, c->spec, c->phi, c->res, c->bbuf, c->R[0], c->R[1], c->R[2],
+                c->lamx, c->lamy, c->spec, c->phi, c->bbuf, c->R[0], c->R[1], c->R[2],
                 c->R[3], c->cntab, c->pa32, c->pc32, c->lowslot, c->low_modes, c->low_scratch, c->scal,
-                c->part, c->part2};
+                c->part, c->part2, c->part3};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -179,7 +179,7 @@ size_t afid_workspace_bytes(const afid_grid_desc* d) {
   const bool mixed = d->precision == AFID_MIXED;
   size_t b = spec_elems(d) * (mixed ? 8 : 16) + tab * 8 + (mixed ? tab * 4 : 0);
   b += n * 8;                                   // phi
-  if (mixed) b += 2 * n * 8;                    // residual + kept rhs
+  if (mixed) b += n * 8;                        // kept rhs
   if (!(d->flags & AFID_POISSON_ONLY)) b += 2 * n * 8 + 2 * nf * 8;  // R buffers
   return b;
 }
@@ -311,7 +311,6 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   c->spec = mixed ? (void*)A.get<float2>(se) : (void*)A.get<double2>(se);
   c->phi = A.get<double>(n);
   if (mixed) {
-    c->res = A.get<double>(n);
     c->bbuf = A.get<double>(n);
     c->pa32 = A.get<float>(nz);
     c->pc32 = A.get<float>(nz);
@@ -331,6 +330,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   if (mixed) {
     c->part2_len = c2r_blocks(g);
     c->part2 = A.get<double>((size_t)2 * c->part2_len);
+    c->part3 = A.get<double>((size_t)3 * c->part2_len);
   }
   if (!A.ok) {
     free_all(c);

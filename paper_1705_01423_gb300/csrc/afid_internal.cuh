@@ -114,7 +114,6 @@ struct afid_ctx {
   void* spec;
   // physical workspace
   double* phi;    // [nz][ny][nx]
-  double* res;    // mixed residual [nz][ny][nx]
   double* bbuf;   // mixed: FP64 right-hand side kept for the residual [nz][ny][nx]
   double* R[4];   // substep right-hand sides (u, v: cells; w, T: faces)
   double* cntab;  // Crank-Nicolson factor tables [3][4][nz+1]
@@ -129,8 +128,9 @@ struct afid_ctx {
   double* scal;   // device scalars (Scalar enum)
   double* part;   // reduction partials
   int part_len;
-  double* part2;  // mixed: per-block (||delta||^2, ||phi||^2) of the accumulate pass
+  double* part2;  // mixed: per-block (||delta||^2, sum dzc delta) of the accumulate pass
   int part2_len;
+  double* part3;  // mixed: per-block partials of the forward pass (stats of b / ||r||^2)
   size_t bytes;
   long long launches;
   afid::Prof* prof;
@@ -158,6 +158,13 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
 int c2r_blocks(const Grid& g);
 // Mixed-precision refined solve of L phi = b (FP64 b, resident) into phi.
 cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi, bool stats);
+// One FP32 spectral solve of the refinement: b (first) or the FP64 residual
+// (b - mean) - L phi_in, formed in the forward transform; phi = delta (first)
+// or phi += delta - mean_W(phi).
+cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_in, double* phi,
+                                const double* skip, bool first, bool stats);
+// Reduction of the stats of b taken by the first forward transform.
+cudaError_t bstats_final(afid_ctx* c);
 // b = D(u, v, w) / s (s from S_PROJ_S)
 cudaError_t divergence_to(afid_ctx* c, const double* u, const double* v, const double* w, double* b);
 // projection with s, beta read from S_PROJ_S / S_PROJ_BETA

@@ -323,30 +323,9 @@ cudaError_t cn_sweeps_adjoint(afid_ctx* c, double* gu, double* gv, double* gw, d
 // r = (b - mean_W b) - L phi, the convergence test on the correction norms,
 // and the final FP64 gauge (zero weighted mean of phi: the residual cannot
 // see a constant, so the FP32 corrections' gauge round-off is removed here).
-__global__ void k_bstats_partial(Grid g, Metric m, const double* __restrict__ b, double* part,
-                                 int stats) {
-  double sw = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int row = blockIdx.x; row < g.nz * g.ny; row += gridDim.x) {
-    const double* br = b + (size_t)row * g.nx;
-    double rs = 0.0;
-    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
-      const double v = br[i];
-      rs += v;
-      if (stats) s2 = fma(v, v, s2);  // norms only for the report
-    }
-    sw = fma(m.dzc[row / g.ny], rs, sw);
-    s1 += rs;
-  }
-  sw = block_sum(sw);
-  s1 = block_sum(s1);
-  s2 = block_sum(s2);
-  if (threadIdx.x == 0) {
-    part[3 * blockIdx.x] = sw;
-    part[3 * blockIdx.x + 1] = s1;
-    part[3 * blockIdx.x + 2] = s2;
-  }
-}
-
+// Reduction of the per-block partials of the first mixed-precision forward
+// transform (k_r2c_x32<R32_FIRST>): weighted mean of b and ||b - mean||^2;
+// resets the refinement's scalars.
 __global__ void k_bstats_final(Grid g, Metric m, const double* part, int np, double* scal) {
   double sw = 0.0, s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) {
@@ -365,44 +344,18 @@ __global__ void k_bstats_final(Grid g, Metric m, const double* part, int np, dou
     scal[S_BMEAN] = mean;
     scal[S_BNORM2] = s2 - 2.0 * mean * s1 + n * mean * mean;
     scal[S_RNORM2] = scal[S_BNORM2];
-    scal[S_CONVERGED] = 0.0;
     scal[S_ITERS] = 0.0;
     scal[S_DNORM2] = 0.0;
     scal[S_ERREST] = 1.0;
+    scal[S_PHIMEAN] = 0.0;
   }
 }
 
-// r = (b - mean) - L phi, FP64 7-point operator; per-block sum of r^2.
-__global__ void k_residual(Grid g, Metric m, const double* __restrict__ b,
-                           const double* __restrict__ phi, double* __restrict__ r, double* part,
-                           const double* scal, int stats) {
-  if (scal[S_CONVERGED] != 0.0) return;
-  const size_t NXY = (size_t)g.nx * g.ny;
-  const double mean = scal[S_BMEAN];
-  double s = 0.0;
-  for (int row = blockIdx.x; row < g.nz * g.ny; row += gridDim.x) {
-    const int k = row / g.ny, j = row - k * g.ny;
-    const size_t r0 = (size_t)row * g.nx;
-    const size_t rjp = ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * g.nx;
-    const size_t rjm = ((size_t)k * g.ny + ((j - 1) & (g.ny - 1))) * g.nx;
-    const double pc = m.pc[k], pa = m.pa[k], pd = m.pdiag[k];
-    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
-      const size_t c = r0 + i;
-      const double f = phi[c];
-      const double sx = phi[r0 + ((i + 1) & (g.nx - 1))] + phi[r0 + ((i - 1) & (g.nx - 1))];
-      const double sy = phi[rjp + i] + phi[rjm + i];
-      double L = sx * g.rdx2;
-      L = fma(sy, g.rdy2, L);
-      if (k < g.nz - 1) L = fma(pc, phi[c + NXY], L);
-      if (k > 0) L = fma(pa, phi[c - NXY], L);
-      L = fma(-pd, f, L);
-      const double rv = (b[c] - mean) - L;
-      r[c] = rv;
-      if (stats) s = fma(rv, rv, s);
-    }
-  }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+cudaError_t bstats_final(afid_ctx* c) {
+  ProfScope ps(c, KF_REFINE);
+  k_bstats_final<<<1, 1024, 0, c->stream>>>(c->g, c->m, c->part3, c2r_blocks(c->g), c->scal);
+  c->launches++;
+  return cudaGetLastError();
 }
 
 // Convergence test after correction k (iterations counted here). The stopping
@@ -422,17 +375,17 @@ __global__ void k_refine_check(Grid g, Metric m, const double* part, int np, con
   }
   const bool have_r = scal[S_ITERS] > 0.5;
   if (have_r)
-    for (int i = threadIdx.x; i < np; i += blockDim.x) rs += part[i];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) rs += part[3 * i];
   d2 = block_sum(d2);
   ps = block_sum(ps);
   rs = block_sum(rs);
   if (threadIdx.x == 0) {
     double swz = 0.0;
     for (int k = 0; k < g.nz; ++k) swz += m.dzc[k];
-    // the first accumulate pass sums dzc * phi (= delta_1) in FP64, later ones
-    // sum dzc * delta_k: the weighted mean of phi accumulates
+    // every accumulate pass removes the mean measured after the previous one
+    // and sums dzc * delta_k: the weighted mean of phi is now that of delta_k
     const double dm = ps / (swz * (double)g.nx * (double)g.ny);
-    scal[S_PHIMEAN] = scal[S_ITERS] < 0.5 ? dm : scal[S_PHIMEAN] + dm;
+    scal[S_PHIMEAN] = dm;
     if (have_r) scal[S_RNORM2] = rs;
     scal[S_ITERS] += 1.0;
     const double k = scal[S_ITERS];
@@ -450,7 +403,11 @@ __global__ void k_refine_check(Grid g, Metric m, const double* part, int np, con
   }
 }
 
+// Final FP64 gauge when the refinement stopped without converging (after a
+// converged refinement the mean left is that of the last, tiny, correction's
+// rounding and the kernel returns at once).
 __global__ void k_sub_mean(Grid g, double* __restrict__ phi, const double* __restrict__ scal) {
+  if (scal[S_CONVERGED] != 0.0) return;
   const size_t n2 = (size_t)g.nx * g.ny * g.nz / 2;  // nx is even
   const double pm = scal[S_PHIMEAN];
   double2* p2 = reinterpret_cast<double2*>(phi);
@@ -463,43 +420,28 @@ __global__ void k_sub_mean(Grid g, double* __restrict__ phi, const double* __res
   }
 }
 
-cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, const double* skip,
-                                bool first);
-
 // Mixed-precision refined solve (device-side convergence test, no host sync):
-//   stats of b (mean_W b, ||b - mean||^2)
-//   k = 1: phi = FP32-solve(b)
-//   k = 2..max: r = (b - mean) - L phi (FP64), phi += FP32-solve(r)
-//   after every correction: convergence test on the correction norms
-//   finally phi -= mean_W(phi) in FP64.
+//   k = 1: phi = FP32-solve(b), with the FP64 stats of b (mean_W b, ||b||)
+//          taken in the same forward transform;
+//   k = 2..max: phi += FP32-solve(r), r = (b - mean) - L phi in FP64, formed
+//          inside the forward transform;
+//   after every correction: convergence test on the correction norms; the
+//   gauge (zero weighted mean) is carried by the accumulate passes.
 // Every kernel returns at once once the test has passed.
 cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi, bool stats) {
   const Grid& g = c->g;
-  const int nb = c->part_len;
   cudaError_t e;
-  {
-    ProfScope ps(c, KF_REFINE);
-    k_bstats_partial<<<nb, 256, 0, c->stream>>>(g, c->m, b, c->part, stats ? 1 : 0);
-    k_bstats_final<<<1, 1024, 0, c->stream>>>(g, c->m, c->part, nb, c->scal);
-    c->launches += 2;
-    if ((e = cudaGetLastError())) return e;
-  }
+  if ((e = cudaMemsetAsync(c->scal + S_CONVERGED, 0, sizeof(double), c->stream))) return e;
+  const int np2 = c->part2_len;
   for (int it = 0; it < c->max_iter; ++it) {
-    if (it > 0) {
-      ProfScope ps(c, KF_REFINE);
-      k_residual<<<nb, 256, 0, c->stream>>>(g, c->m, b, phi, c->res, c->part, c->scal, stats ? 1 : 0);
-      c->launches++;
-    }
-    if ((e = spectral_solve_fp32(c, it == 0 ? b : c->res, phi, c->scal + S_CONVERGED, it == 0)))
-      return e;
+    if ((e = spectral_solve_fp32(c, b, phi, phi, c->scal + S_CONVERGED, it == 0, stats))) return e;
     ProfScope ps(c, KF_REFINE);
-    k_refine_check<<<1, 1024, 0, c->stream>>>(g, c->m, c->part, nb, c->part2, c->part2_len,
-                                              c->scal, c->tol);
+    k_refine_check<<<1, 1024, 0, c->stream>>>(g, c->m, c->part3, np2, c->part2, np2, c->scal, c->tol);
     c->launches++;
     if ((e = cudaGetLastError())) return e;
   }
   ProfScope ps(c, KF_REFINE);
-  k_sub_mean<<<nb, 256, 0, c->stream>>>(g, phi, c->scal);
+  k_sub_mean<<<c->part_len, 256, 0, c->stream>>>(g, phi, c->scal);
   c->launches++;
   return cudaGetLastError();
 }

@@ -81,6 +81,28 @@ template <> __device__ __forceinline__ double to_double<float>(float x) {
   return __longlong_as_double((long long)bits);
 }
 
+// s += x with the exact rounding error of the addition (Knuth's TwoSum, with
+// the round-to-nearest intrinsics so that no step is contracted or
+// re-associated) added to the compensation c.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float xp = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, xp)), __fsub_rn(x, xp));
+  s = t;
+  c = __fadd_rn(c, e);
+}
+__device__ __forceinline__ void two_sum_acc(double& s, double& c, double x) {
+  const double t = __dadd_rn(s, x);
+  const double xp = __dsub_rn(t, s);
+  const double e = __dadd_rn(__dsub_rn(s, __dsub_rn(t, xp)), __dsub_rn(x, xp));
+  s = t;
+  c = __dadd_rn(c, e);
+}
+
+// Product rounded on its own (never fused into a following add).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename R> __device__ __forceinline__ R to_real(double x);
 template <> __device__ __forceinline__ double to_real<double>(double x) { return x; }
 template <> __device__ __forceinline__ float to_real<float>(double x) {
@@ -187,18 +209,172 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
 }
 
 // --------------------------------------------------------------------------
+// Mixed precision forward x transform: FP64 input line -> FP32 spectrum, no
+// FP64 arithmetic per point except where the refinement needs it.
+//   R32_FIRST: line = b. FP64 per-block partial sums of dzc*b and b (and of
+//              b^2 and max |b| with stats) for the weighted mean removed from
+//              b (solvability) and the reported norm: part[3 blk + 0..2].
+//   R32_RESID: line = r = (b - mean_W b) - L phi, the refinement's FP64
+//              residual, computed on the fly (7-point operator of Sec. 2.2;
+//              8 FP64 operations per point); with stats the per-block ||r||^2
+//              (FP32, report only) in part[3 blk].
+// Same line transform and unpacking as k_r2c_x.
+enum { R32_FIRST = 0, R32_RESID = 1 };
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;  // valid on thread 0
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double* __restrict__ b,
+                                                 const double* __restrict__ phi, float2* __restrict__ spec,
+                                                 const float2* __restrict__ tw, double* __restrict__ scal,
+                                                 double* __restrict__ part, int stats,
+                                                 const double* __restrict__ skip) {
+  if (skip && *skip != 0.0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[16];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  const int M = g.M, T = M / 8;
+  const int lines = blockDim.x / T;
+  const int line = threadIdx.x / T, t = threadIdx.x - line * T;
+  const int nrows = g.nz * g.ny;
+  const int row = blockIdx.x * lines + line;
+  const bool active = row < nrows;
+  const int stride = pad8(M) + 1;
+  float2* buf = sm + line * stride;
+  float2* stw = sm + lines * stride;  // twiddle table, nx entries
+  for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
+  double s_row = 0.0, s2 = 0.0;
+  float rr = 0.f;
+  unsigned long long amax = 0ull;
+  int k = 0;
+  if (active) {
+    const int nx = g.nx;
+    k = row / g.ny;
+    const size_t r0 = (size_t)row * nx;
+    if (MODE == R32_FIRST) {
+      const double2* s = reinterpret_cast<const double2*>(b + r0);
+      for (int n = t; n < M; n += T) {
+        const double2 x = s[n];
+        s_row += x.x + x.y;
+        if (stats) {
+          s2 = fma(x.x, x.x, s2);
+          s2 = fma(x.y, x.y, s2);
+          const unsigned long long ax = (unsigned long long)__double_as_longlong(x.x) & 0x7fffffffffffffffull;
+          const unsigned long long ay = (unsigned long long)__double_as_longlong(x.y) & 0x7fffffffffffffffull;
+          amax = max(amax, max(ax, ay));
+        }
+        buf[pad8(n)] = make_float2(to_real<float>(x.x), to_real<float>(x.y));
+      }
+    } else {
+      const int j = row - k * g.ny;
+      const size_t NXY = (size_t)nx * g.ny;
+      const size_t rjp = ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * nx;
+      const size_t rjm = ((size_t)k * g.ny + ((j - 1) & (g.ny - 1))) * nx;
+      const double pc = m.pc[k], pa = m.pa[k], pd = m.pdiag[k];
+      const double mean = scal[S_BMEAN];
+      const double ax = -g.rdx2, ay = -g.rdy2;
+      const bool up = k < g.nz - 1, dn = k > 0;
+      for (int n = t; n < M; n += T) {
+        const int i = 2 * n;
+        const double2 f = *reinterpret_cast<const double2*>(phi + r0 + i);
+        const double fw = phi[r0 + ((i - 1) & (nx - 1))];
+        const double fe = phi[r0 + ((i + 2) & (nx - 1))];
+        const double2 fn = *reinterpret_cast<const double2*>(phi + rjp + i);
+        const double2 fs = *reinterpret_cast<const double2*>(phi + rjm + i);
+        const double2 bb = *reinterpret_cast<const double2*>(b + r0 + i);
+        // r = (b - mean) + pdiag phi - rdx2 (phi_w + phi_e) - rdy2 (phi_s + phi_n)
+        //     - pc phi_up - pa phi_down
+        double rx = fma(pd, f.x, bb.x - mean);
+        double ry = fma(pd, f.y, bb.y - mean);
+        rx = fma(ax, fw + f.y, rx);
+        ry = fma(ax, f.x + fe, ry);
+        rx = fma(ay, fn.x + fs.x, rx);
+        ry = fma(ay, fn.y + fs.y, ry);
+        if (up) {
+          const double2 fu = *reinterpret_cast<const double2*>(phi + r0 + NXY + i);
+          rx = fma(-pc, fu.x, rx);
+          ry = fma(-pc, fu.y, ry);
+        }
+        if (dn) {
+          const double2 fd = *reinterpret_cast<const double2*>(phi + r0 - NXY + i);
+          rx = fma(-pa, fd.x, rx);
+          ry = fma(-pa, fd.y, ry);
+        }
+        const float2 r32 = make_float2(to_real<float>(rx), to_real<float>(ry));
+        if (stats) rr = fmaf(r32.x, r32.x, fmaf(r32.y, r32.y, rr));
+        buf[pad8(n)] = r32;
+      }
+    }
+  }
+  __syncthreads();
+  fft_line<false>(buf, M, stw, 2, t, active);
+  if (active) {
+    float2* out = spec + (size_t)row * g.P;
+    for (int q = t; q <= M / 2; q += T) {
+      const float2 zk = buf[pad8(q)];
+      if (q == 0) {
+        out[0] = make_float2(zk.x + zk.y, 0.f);
+        out[M] = make_float2(zk.x - zk.y, 0.f);
+        continue;
+      }
+      const float2 zm = buf[pad8(M - q)];
+      const float2 E = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
+      const float2 O = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
+      const float2 wO = cmul(O, stw[q]);
+      out[q] = cadd(E, wO);
+      if (q != M / 2) out[M - q] = cconj(csub(E, wO));
+    }
+  }
+  if (MODE == R32_FIRST) {
+    const double sw = active ? m.dzc[k] * s_row : 0.0;
+    const double a = block_sum_d(sw, red);
+    const double c = block_sum_d(s_row, red);
+    const double d = stats ? block_sum_d(s2, red) : 0.0;
+    if (threadIdx.x == 0) {
+      part[3 * blockIdx.x] = a;
+      part[3 * blockIdx.x + 1] = c;
+      part[3 * blockIdx.x + 2] = d;
+    }
+    if (stats) {
+      for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if ((threadIdx.x & 31) == 0 && amax > 0ull)
+        atomicMax(reinterpret_cast<unsigned long long*>(scal + S_RHS_ABSMAX), amax);
+    }
+  } else if (stats) {
+    const double a = block_sum_d(to_double(rr), red);
+    if (threadIdx.x == 0) part[3 * blockIdx.x] = a;
+  }
+}
+
+// --------------------------------------------------------------------------
 // Inverse x transform: X_k, k = 0..M -> nx reals (imaginary parts of X_0 and
 // X_M are ignored). Z'_k = E'_k + i O'_k with E'_k = X_k + conj X_{M-k},
 // O'_k = (X_k - conj X_{M-k}) conj(w_k); an inverse M-point FFT gives
 // nx (x_2n + i x_2n+1) before the 1/(nx ny) normalisation `scale`.
-// ACC = 0 writes phi, ACC = 1 adds to phi.
+// MODE 0 writes phi = scale * x (FP64 path). Mixed precision, with per-block
+// partials part[2 blk] = ||delta||^2 (FP32 per thread) and part[2 blk + 1] =
+// sum dzc * delta (FP32 per thread, compensated in MODE 2):
+//   MODE 2 writes phi = delta (the first correction);
+//   MODE 1 adds phi += delta - mean_W(phi) (the mean measured after the
+//   previous correction), so that the gauge of phi is kept as it is refined.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
                                                const typename cplx<R>::T* __restrict__ spec,
                                                const typename cplx<R>::T* __restrict__ tw,
                                                double scale, double* __restrict__ phi,
                                                const double* __restrict__ skip,
-                                               double* __restrict__ part) {
+                                               double* __restrict__ part,
+                                               const double* __restrict__ pmean) {
   using C = typename cplx<R>::T;
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -235,31 +411,41 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
   }
   __syncthreads();
   fft_line<true>(buf, M, stw, 2, t, active);
-  R d2 = (R)0, dsum = (R)0;
+  R d2 = (R)0, dsum = (R)0, dcomp = (R)0;
   double psum = 0.0;
   if (active) {
     double2* o2 = reinterpret_cast<double2*>(phi + (size_t)row * g.nx);
     const R sc = (R)scale;
+    // MODE 1 removes the weighted mean of phi measured after the previous
+    // correction (rounded to the working precision) while adding this one
+    const R pm = MODE == 1 ? to_real<R>(*pmean) : (R)0;
     for (int n = t; n < M; n += T) {
       const C z = buf[pad8(n)];
       if (MODE == 0) {
         o2[n] = make_double2((double)z.x * scale, (double)z.y * scale);
       } else {
-        const R dx = z.x * sc, dy = z.y * sc;
+        // rounded products (no contraction into the sums below): the sums
+        // must see exactly the values stored in phi
+        const R dx = mul_rn(z.x, sc), dy = mul_rn(z.y, sc);
         d2 += dx * dx + dy * dy;
-        double2 r = make_double2(to_double(dx), to_double(dy));
         if (MODE == 1) {        // later corrections are small: their sum in FP32
+          double2 r = make_double2(to_double(dx - pm), to_double(dy - pm));
           const double2 old = o2[n];
           r.x += old.x;
           r.y += old.y;
+          o2[n] = r;
           dsum += dx + dy;
-        } else {                // the first correction is the bulk of phi: FP64 sum
-          psum += r.x + r.y;
+        } else {                // the first correction is the bulk of phi:
+          o2[n] = make_double2(to_double(dx), to_double(dy));
+          // compensated FP32 sum: exact rounding error of every addition
+          // (TwoSum) collected in dcomp
+          two_sum_acc(dsum, dcomp, dx);
+          two_sum_acc(dsum, dcomp, dy);
         }
-        o2[n] = r;
       }
     }
-    psum = (MODE == 1 ? to_double(dsum) : psum) * m.dzc[row / g.ny];
+    if (MODE == 1) psum = to_double(dsum) * m.dzc[row / g.ny];
+    if (MODE == 2) psum = (to_double(dsum) + to_double(dcomp)) * m.dzc[row / g.ny];
   }
   if (MODE != 0) {
     // per-block ||delta||^2 and sum of dzc * phi (weighted mean of phi)
@@ -332,6 +518,60 @@ __global__ void __launch_bounds__(1024) k_fft_y(Grid g, typename cplx<R>::T* __r
 // d'_k = (d_k - a_k d'_{k-1}) m_k stored in place, back substitution
 // x_k = d'_k - c_k m_k x_{k+1}. The (0,0) mode is left to k_zero_mode; in
 // mixed precision the low modes (lambda < lam_thr) are left to k_thomas_low.
+// Forward elimination and back substitution of one column (rows k = 0..nz-1,
+// pa[0] = 0), with the loads of the next U rows issued together so that the
+// memory latency is paid once per U rows rather than once per row (U = 8 in
+// FP32, which is bound by memory latency; 4 in FP64, bound by the FP64 pipe,
+// where more registers per thread would cost resident threads).
+template <typename R, typename C>
+__device__ __forceinline__ void thomas_column(C* __restrict__ col, const R* __restrict__ mt,
+                                              const R* __restrict__ pa, const R* __restrict__ pc,
+                                              int nz, size_t plane, size_t tplane) {
+  constexpr int U = sizeof(R) == 4 ? 8 : 4;
+  C dv[U];
+  R mv[U];
+  C dp = C{(R)0, (R)0};
+  for (int kb = 0; kb < nz; kb += U) {
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int k = kb + q;
+      if (k < nz) {
+        dv[q] = col[k * plane];
+        mv[q] = mt[k * tplane];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int k = kb + q;
+      if (k < nz) {
+        const R ak = pa[k];
+        dp = C{(dv[q].x - ak * dp.x) * mv[q], (dv[q].y - ak * dp.y) * mv[q]};
+        col[k * plane] = dp;
+      }
+    }
+  }
+  C x = dp;
+  for (int kb = nz - 2; kb >= 0; kb -= U) {
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int k = kb - q;
+      if (k >= 0) {
+        dv[q] = col[k * plane];
+        mv[q] = mt[k * tplane];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int k = kb - q;
+      if (k >= 0) {
+        const R cp = pc[k] * mv[q];
+        x = C{dv[q].x - cp * x.x, dv[q].y - cp * x.y};
+        col[k * plane] = x;
+      }
+    }
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(128) k_thomas(Grid g, Metric m, typename cplx<R>::T* __restrict__ spec,
                                                 const R* __restrict__ mtab,
@@ -351,27 +591,7 @@ __global__ void __launch_bounds__(128) k_thomas(Grid g, Metric m, typename cplx<
   const size_t tplane = (size_t)g.nyh * W;
   C* col = spec + (size_t)ky * g.P + kx;
   const R* mt = mtab + (size_t)kyh * W + kx;
-  const int nz = g.nz;
-  C d = col[0];
-  R mk = mt[0];
-  C dp = C{d.x * mk, d.y * mk};
-  col[0] = dp;
-#pragma unroll 4
-  for (int k = 1; k < nz; ++k) {
-    d = col[k * plane];
-    mk = mt[k * tplane];
-    const R ak = pa[k];
-    dp = C{(d.x - ak * dp.x) * mk, (d.y - ak * dp.y) * mk};
-    col[k * plane] = dp;
-  }
-  C x = dp;
-#pragma unroll 4
-  for (int k = nz - 2; k >= 0; --k) {
-    const C e = col[k * plane];
-    const R cp = pc[k] * mt[k * tplane];
-    x = C{e.x - cp * x.x, e.y - cp * x.y};
-    col[k * plane] = x;
-  }
+  thomas_column<R, C>(col, mt, pa, pc, g.nz, plane, tplane);
 }
 
 // Mixed precision: FP32 sweeps for most modes; the nearly singular low modes
@@ -397,26 +617,7 @@ __global__ void __launch_bounds__(128) k_thomas_mixed(Grid g, Metric m, float2* 
   const int nz = g.nz;
   if (lowslot[(size_t)ky * W + kx] >= 0) return;  // FP64 warp solver (k_tridiag_warp)
   const float* mt = mtab32 + (size_t)kyh * W + kx;
-  float2 d = col[0];
-  float mk = mt[0];
-  float2 dp = make_float2(d.x * mk, d.y * mk);
-  col[0] = dp;
-#pragma unroll 4
-  for (int k = 1; k < nz; ++k) {
-    d = col[k * plane];
-    mk = mt[k * tplane];
-    const float ak = pa32[k];
-    dp = make_float2((d.x - ak * dp.x) * mk, (d.y - ak * dp.y) * mk);
-    col[k * plane] = dp;
-  }
-  float2 x = dp;
-#pragma unroll 4
-  for (int k = nz - 2; k >= 0; --k) {
-    const float2 e = col[k * plane];
-    const float cp = pc32[k] * mt[k * tplane];
-    x = make_float2(e.x - cp * x.x, e.y - cp * x.y);
-    col[k * plane] = x;
-  }
+  thomas_column<float, float2>(col, mt, pa32, pc32, nz, plane, tplane);
 }
 
 // --------------------------------------------------------------------------
@@ -766,7 +967,7 @@ static cudaError_t run_c2r(afid_ctx* c, const typename cplx<R>::T* spec,
   const double scale = 1.0 / ((double)g.nx * (double)g.ny);
   auto kf = mode == 1 ? k_c2r_x<R, 1> : (mode == 2 ? k_c2r_x<R, 2> : k_c2r_x<R, 0>);
   cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, spec, tw, scale, phi, skip, part);
+  kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, spec, tw, scale, phi, skip, part, c->scal + S_PHIMEAN);
   c->launches++;
   return cudaGetLastError();
 }
@@ -813,12 +1014,24 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
 // FP32 spectral solve of `src` (FP64) for the mixed-precision refinement:
 // phi = delta (first) or phi += delta, with per-block partials of ||delta||^2
 // and of sum dzc phi in c->part2; every kernel returns at once when *skip != 0.
-cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, const double* skip,
-                                bool first) {
+cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_in, double* phi,
+                                const double* skip, bool first, bool stats) {
   const Grid& g = c->g;
   float2* spec = static_cast<float2*>(c->spec);
   cudaError_t e;
-  if ((e = run_r2c<float>(c, src, nullptr, nullptr, nullptr, false, spec, c->twx32, 0, skip))) return e;
+  {
+    ProfScope ps(c, KF_R2C);
+    const int T = g.M / 8, lines = r2c_lines<float>(g);
+    const size_t sm = (size_t)lines * line_smem<float>(g.M) + (size_t)g.nx * sizeof(float2);
+    const int blocks = ceil_div((long long)g.nz * g.ny, lines);
+    auto kf = first ? k_r2c_x32<R32_FIRST> : k_r2c_x32<R32_RESID>;
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, b, phi_in, spec, c->twx32, c->scal, c->part3,
+                                             stats ? 1 : 0, skip);
+    c->launches++;
+    if ((e = cudaGetLastError())) return e;
+  }
+  if (first && (e = bstats_final(c))) return e;
   if ((e = run_fft_y<float>(c, spec, c->twy32, false, skip))) return e;
   {
     ProfScope ps(c, KF_THOMAS);
@@ -850,9 +1063,6 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* src, double* phi, con
   return run_c2r<float>(c, spec, c->twx32, phi, first ? 2 : 1, skip, c->part2);
 }
 
-}  // namespace afid
-
-namespace afid {
 int c2r_blocks(const Grid& g) {
   const int T = g.M / 8;
   int lines = 256 / T;
