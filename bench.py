@@ -135,10 +135,12 @@ class ClockSampler:
 def fft_ops(n: int) -> float:
     """FP64 operations per complex point of one n-point transform with the
     library's pass sequence (radix 8 first, untwiddled, then twiddled radix-8
-    passes, then one radix-4 or radix-2 pass): 7, 10.5, 7, 4 per point."""
+    passes, then one radix-4 or radix-2 pass): 6.5, 10, 7, 4 per point (a
+    radix-8 butterfly is 52 operations with its 1/sqrt(2) scalings fused into
+    FMAs, a complex twiddle 4)."""
     ops, p = 0.0, 1
     while n // p >= 8:
-        ops += 7.0 if p == 1 else 10.5
+        ops += 6.5 if p == 1 else 10.0
         p *= 8
     if n // p == 4:
         ops += 7.0
@@ -152,18 +154,20 @@ def family_work(fam: str, w):
     (bytes, fp64_ops). Bytes: compulsory HBM traffic of the kernel's own inputs
     and outputs. FP64 operations: the formulation's arithmetic, each add,
     multiply or FMA counted once (per grid point unless noted):
-      r2c_x  divergence 7 + packed real FFT fft_ops(nx/2)/2 + unpacking 4
+      r2c_x  divergence 6 + packed real FFT fft_ops(nx/2)/2 + unpacking 4
       c2r_x  packing 4 + fft_ops(nx/2)/2 + scaling 1
       fft_y  fft_ops(ny) per complex point (nx/2+1 complex per row)
       thomas 7 per complex point (4 forward, 3 backward)
-      project 12; rhs 120 (u 31, v 28, w 35, T 27); crank_nicolson 16 (4 fields);
+      project 9; rhs 108 (shared face fluxes 29, u 19, v 19, w 21, T 17, per-plane
+      factors 3; the recomputed fluxes of the warp- and block-edge neighbours are
+      overhead, not counted); crank_nicolson 16 (4 fields);
       cfl_reduce 7 (|.| is an operand modifier)."""
     nx, ny, nz = w.nx, w.ny, w.nz
     n = nx * ny * nz
     M1 = nx // 2 + 1
     nc = M1 * ny * nz
     if fam == "r2c_x":
-        return 24 * n + 16 * nc, (7 + fft_ops(nx // 2) / 2 + 4) * n
+        return 24 * n + 16 * nc, (6 + fft_ops(nx // 2) / 2 + 4) * n
     if fam == "c2r_x":
         return 16 * nc + 8 * n, (4 + fft_ops(nx // 2) / 2 + 1) * n
     if fam == "fft_y":
@@ -171,9 +175,9 @@ def family_work(fam: str, w):
     if fam == "thomas":
         return 32 * nc + 8 * M1 * (ny // 2 + 1) * nz, 7 * nc
     if fam == "project":
-        return 72 * n, 12 * n
+        return 72 * n, 9 * n
     if fam == "rhs":
-        return 136 * n, 120 * n
+        return 136 * n, 108 * n
     if fam == "crank_nicolson":
         return 4 * 24 * n, 16 * n
     if fam == "cfl_reduce":

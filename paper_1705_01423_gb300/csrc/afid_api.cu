@@ -323,7 +323,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     c->R[2] = A.get<double>(nf);
     c->R[3] = A.get<double>(nf);
   }
-  c->cntab = A.get<double>((size_t)3 * 4 * (nz + 1));
+  c->cntab = A.get<double>((size_t)3 * CN_TAB_ARRAYS * (nz + 1));
   c->scal = A.get<double>(S_COUNT);
   c->part_len = c->num_sms * 8;
   c->part = A.get<double>((size_t)3 * c->part_len);
@@ -365,7 +365,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   }
   ok = ok && cudaMemset(c->spec, 0, se * (mixed ? sizeof(float2) : sizeof(double2))) == cudaSuccess;
   ok = ok && cudaMemset(c->scal, 0, S_COUNT * sizeof(double)) == cudaSuccess;
-  ok = ok && cudaMemset(c->cntab, 0, (size_t)3 * 4 * (nz + 1) * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMemset(c->cntab, 0, (size_t)3 * CN_TAB_ARRAYS * (nz + 1) * sizeof(double)) == cudaSuccess;
   ok = ok && init_thomas_tables(c) == cudaSuccess;
   ok = ok && ((c->flags & AFID_NO_TMA) || init_ffty_tma(c) == cudaSuccess);
   ok = ok && cudaStreamSynchronize(c->stream) == cudaSuccess;

@@ -75,6 +75,9 @@ struct Prof {
   long long n[KF_COUNT] = {};
 };
 
+// Arrays per variable set in the Crank-Nicolson table (k_cn_tables).
+constexpr int CN_TAB_ARRAYS = 7;
+
 struct Grid {
   int nx, ny, nz;
   int M;         // nx / 2
@@ -116,7 +119,7 @@ struct afid_ctx {
   double* phi;    // [nz][ny][nx]
   double* bbuf;   // mixed: FP64 right-hand side kept for the residual [nz][ny][nx]
   double* R[4];   // substep right-hand sides (u, v: cells; w, T: faces)
-  double* cntab;  // Crank-Nicolson factor tables [3][4][nz+1]
+  double* cntab;  // Crank-Nicolson factor tables [3][CN_TAB_ARRAYS][nz+1]
   // mixed precision: FP32 copies of the Poisson off-diagonals; the low modes
   // solved in FP64 by the warp solver: their list (ky, kx) and a mask
   // lowslot[ky][kx] (>= 0 for a low mode) that the FP32 sweep skips

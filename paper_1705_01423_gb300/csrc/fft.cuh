@@ -60,25 +60,27 @@ template <bool INV, typename C> __device__ __forceinline__ void dft8(C* a) {
   // even / odd halves
   dft4<INV>(a[0], a[2], a[4], a[6]);
   dft4<INV>(a[1], a[3], a[5], a[7]);
-  // twiddle the odd half by w8^k, k = 1, 2, 3
+  // twiddle the odd half by w8^k, k = 1, 2, 3; the 1/sqrt(2) of w8 and w8^3
+  // is applied inside the final additions (one FMA each instead of a
+  // multiplication and an addition)
   C o1 = a[3], o2 = a[5], o3 = a[7];
   if (!INV) {
-    o1 = C{(o1.x + o1.y) * h, (o1.y - o1.x) * h};
-    o3 = C{(o3.y - o3.x) * h, -(o3.x + o3.y) * h};
+    o1 = C{o1.x + o1.y, o1.y - o1.x};
+    o3 = C{o3.y - o3.x, -(o3.x + o3.y)};
   } else {
-    o1 = C{(o1.x - o1.y) * h, (o1.x + o1.y) * h};
-    o3 = C{-(o3.x + o3.y) * h, (o3.x - o3.y) * h};
+    o1 = C{o1.x - o1.y, o1.x + o1.y};
+    o3 = C{-(o3.x + o3.y), o3.x - o3.y};
   }
   o2 = rot_mi<INV>(o2);
   C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6], o0 = a[1];
   a[0] = cadd(e0, o0);
   a[4] = csub(e0, o0);
-  a[1] = cadd(e1, o1);
-  a[5] = csub(e1, o1);
+  a[1] = C{fma(o1.x, h, e1.x), fma(o1.y, h, e1.y)};
+  a[5] = C{fma(-o1.x, h, e1.x), fma(-o1.y, h, e1.y)};
   a[2] = cadd(e2, o2);
   a[6] = csub(e2, o2);
-  a[3] = cadd(e3, o3);
-  a[7] = csub(e3, o3);
+  a[3] = C{fma(o3.x, h, e3.x), fma(o3.y, h, e3.y)};
+  a[7] = C{fma(-o3.x, h, e3.x), fma(-o3.y, h, e3.y)};
 }
 
 // Shared-memory slot of point m of a line: padded line (one slot every 8

@@ -50,28 +50,78 @@ static inline dim3 point_grid(const Grid& g, int nzp, int& bx) {
 // Projection and pressure update:
 //   u -= s (phi_i - phi_{i-1})/dx, v -= s (phi_j - phi_{j-1})/dy,
 //   w_k -= s (phi_k - phi_{k-1})/dzf_k (interior faces),
-//   p += phi - beta [pc_k (phi_{k+1} - phi_k) - pa_k (phi_k - phi_{k-1})].
-__global__ void k_project(Grid g, Metric m, double* __restrict__ u, double* __restrict__ v,
-                          double* __restrict__ w, double* __restrict__ p,
-                          const double* __restrict__ phi, const double* __restrict__ scal) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+//   p += phi - beta [pc_k (phi_{k+1} - phi_k) - pa_k (phi_k - phi_{k-1})]
+//      = p + (1 + beta (pa_k + pc_k)) phi_k - beta pc_k phi_{k+1} - beta pa_k phi_{k-1}
+// (pa_0 = pc_{nz-1} = 0: zero-flux walls). One thread per (x, y) column
+// marches over a chunk of k with phi_{k-1}, phi_k, phi_{k+1} in registers;
+// the per-row factors are formed once per block in shared memory, which
+// leaves 9 FP64 operations per point (this part issues 2 FP64 operations per
+// clock per SM, so the count, not HBM, sets the time).
+__global__ void __launch_bounds__(256) k_project(Grid g, Metric m, double* __restrict__ u,
+                                                 double* __restrict__ v, double* __restrict__ w,
+                                                 double* __restrict__ p, const double* __restrict__ phi,
+                                                 const double* __restrict__ scal, int kchunk) {
+  extern __shared__ double pco[];  // [4][kchunk]: s/dzf, 1 + beta (pa + pc), beta pc, beta pa
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * blockDim.x + tx, j = blockIdx.y * blockDim.y + ty;
+  const int k0 = blockIdx.z * kchunk, k1 = min(g.nz, k0 + kchunk);
   const double s = scal[S_PROJ_S], beta = scal[S_PROJ_BETA];
+  double* sz = pco;
+  double* bd = pco + kchunk;
+  double* bc = pco + 2 * kchunk;
+  double* ba = pco + 3 * kchunk;
+  for (int q = ty * blockDim.x + tx; q < k1 - k0; q += blockDim.x * blockDim.y) {
+    const int k = k0 + q;
+    sz[q] = s * m.rdzf[k];
+    const double bpc = beta * m.pc[k], bpa = beta * m.pa[k];
+    bc[q] = bpc;
+    ba[q] = bpa;
+    bd[q] = 1.0 + (bpc + bpa);
+  }
+  __syncthreads();
+  const double sx = s * g.rdx, sy = s * g.rdy;
+  const size_t NXY = (size_t)g.nx * g.ny;
   const int im = (i - 1) & (g.nx - 1), jm = (j - 1) & (g.ny - 1);
-  const size_t c = at(g, k, j, i);
-  const double f = phi[c];
-  const double fkm = k > 0 ? phi[c - (size_t)g.nx * g.ny] : f;
-  const double fkp = k < g.nz - 1 ? phi[c + (size_t)g.nx * g.ny] : f;
-  u[c] -= s * (f - phi[at(g, k, j, im)]) * g.rdx;
-  v[c] -= s * (f - phi[at(g, k, jm, i)]) * g.rdy;
-  if (k > 0) w[c] -= s * (f - fkm) * m.rdzf[k];
-  if (p) p[c] += f - beta * (m.pc[k] * (fkp - f) - m.pa[k] * (f - fkm));
+  const size_t col = (size_t)j * g.nx + i, cim = (size_t)j * g.nx + im, cjm = (size_t)jm * g.nx + i;
+  size_t c = (size_t)k0 * NXY;
+  double f = phi[c + col];
+  double fkm = k0 > 0 ? phi[c - NXY + col] : f;
+#pragma unroll 2
+  for (int k = k0; k < k1; ++k, c += NXY) {
+    const int q = k - k0;
+    const double fkp = k < g.nz - 1 ? phi[c + NXY + col] : f;
+    const double fim = phi[c + cim], fjm = phi[c + cjm];
+    u[c + col] = fma(-sx, f - fim, u[c + col]);
+    v[c + col] = fma(-sy, f - fjm, v[c + col]);
+    if (k > 0) w[c + col] = fma(-sz[q], f - fkm, w[c + col]);
+    if (p) {
+      double pv = fma(bd[q], f, p[c + col]);
+      pv = fma(-bc[q], fkp, pv);
+      pv = fma(-ba[q], fkm, pv);
+      p[c + col] = pv;
+    }
+    fkm = f;
+    f = fkp;
+  }
 }
 
 cudaError_t project(afid_ctx* c, double* u, double* v, double* w, double* p, const double* phi) {
   ProfScope ps(c, KF_PROJECT);
-  int bx;
-  dim3 grd = point_grid(c->g, c->g.nz, bx);
-  k_project<<<grd, bx, 0, c->stream>>>(c->g, c->m, u, v, w, p, phi, c->scal);
+  const Grid& g = c->g;
+  const int bx = g.nx < 32 ? g.nx : 32, by = g.ny < 8 ? g.ny : 8;
+  // chunks of k so that the grid is several waves of resident blocks
+  const long long bxy = (long long)(g.nx / bx) * (g.ny / by);
+  const long long want = 32LL * c->num_sms;
+  int nch = (int)((want + bxy - 1) / bxy);
+  const int max_ch = g.nz / 8 > 0 ? g.nz / 8 : 1;
+  nch = nch < 1 ? 1 : (nch > max_ch ? max_ch : nch);
+  const int min_ch = (g.nz + 1023) / 1024;  // shared memory <= 32 KB per block
+  nch = nch < min_ch ? min_ch : nch;
+  const int kchunk = (g.nz + nch - 1) / nch;
+  nch = (g.nz + kchunk - 1) / kchunk;
+  dim3 blk(bx, by), grd(g.nx / bx, g.ny / by, nch);
+  k_project<<<grd, blk, (size_t)4 * kchunk * sizeof(double), c->stream>>>(g, c->m, u, v, w, p, phi,
+                                                                         c->scal, kchunk);
   c->launches++;
   return cudaGetLastError();
 }
@@ -190,13 +240,26 @@ cudaError_t cfl(afid_ctx* c, const double* u, const double* v, const double* w, 
 // 1 (faces, nu), 2 (faces, kappa); (I - beta dzz) with beta = alpha_l dt d/2.
 // Row k: sub = -beta a_k, diag = 1 + beta (a_k + c_k), sup = -beta c_k;
 // tab[o][0][k] = sub_k, tab[o][1][k] = m_k = 1/(diag_k - sub_k c'_{k-1}),
-// tab[o][2][k] = c'_k = sup_k m_k, tab[o][3][k] = sup_k. Thread 0 also
-// publishes dt, the projection scale s = alpha_l dt and beta = alpha_l dt nu/2.
-__global__ void k_cn_tables(Grid g, Metric m, int l, double dt_in, double* __restrict__ scal,
-                            double nu, double kappa, double* __restrict__ tab) {
-  const int o = threadIdx.x;
+// tab[o][2][k] = c'_k = sup_k m_k, tab[o][3][k] = sup_k; for the explicit
+// side of the same substep (the alpha_l dt d dzz q term of R) tab[o][4][k] =
+// 2 beta a_k, tab[o][5][k] = 2 beta c_k, tab[o][6][k] = -2 beta (a_k + c_k).
+// Thread 0 also publishes dt, the projection scale s = alpha_l dt and
+// beta = alpha_l dt nu/2.
+// One warp per variable set o. The coefficients of every row are independent
+// and computed by all lanes. The pivots follow from the continuant
+// Q_k = diag_k Q_{k-1} - sub_k sup_{k-1} Q_{k-2} (Q_{k0-1} = 1, Q_{k0-2} = 0):
+// m_k = 1 / (diag_k - sub_k c'_{k-1}) = Q_{k-1} / Q_k and c'_k = sup_k m_k.
+// Its serial chain is one FMA per row (the product with Q_{k-2} is formed a
+// row ahead), run by one lane with a power-of-two rescaling every 8 rows;
+// the divisions then run in parallel over the rows. (On this part a
+// dependent FP64 operation costs tens of cycles, and a division in the chain
+// of the direct recurrence several of them per row.)
+__global__ void __launch_bounds__(96) k_cn_tables(Grid g, Metric m, int l, double dt_in,
+                                                  double* __restrict__ scal, double nu, double kappa,
+                                                  double* __restrict__ tab) {
+  const int o = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double dt = dt_in > 0.0 ? dt_in : scal[S_DT];
-  if (o == 0) {
+  if (threadIdx.x == 0) {
     scal[S_DT] = dt;
     scal[S_PROJ_S] = rk_alpha(l) * dt;
     scal[S_PROJ_BETA] = rk_alpha(l) * dt * nu * 0.5;
@@ -204,44 +267,86 @@ __global__ void k_cn_tables(Grid g, Metric m, int l, double dt_in, double* __res
   if (o >= 3) return;
   const double beta = rk_alpha(l) * dt * (o == 2 ? kappa : nu) * 0.5;
   const int L = g.nz + 1;
-  double* sub = tab + (size_t)o * 4 * L;
+  double* sub = tab + (size_t)o * CN_TAB_ARRAYS * L;
   double* mm = sub + L;
   double* cp = mm + L;
   double* sp = cp + L;
+  double* ea = sp + L;   // explicit-side alpha_l dt d dzz coefficients (RHS)
+  double* ec = ea + L;
+  double* ed = ec + L;
   const int k0 = o == 0 ? 0 : 1, k1 = g.nz;  // rows k0..nz-1
   const double* __restrict__ pa = o == 0 ? m.ca : m.fa;
   const double* __restrict__ pc = o == 0 ? m.cc : m.fc;
-  // The recurrence is serial; the coefficients of the next B rows are loaded
-  // together so that only the pivot chain is on the critical path.
-  constexpr int B = 8;
-  double cprev = 0.0;
-  for (int kb = k0; kb < k1; kb += B) {
-    double av[B], cv[B];
+  // every row's coefficients; diag_k -> mm[k] and sub_k sup_{k-1} -> cp[k]
+  // as the chain's inputs (both overwritten by it)
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const double a = pa[k], c = pc[k];
+    const double sk = -beta * a;
+    sub[k] = sk;
+    sp[k] = -beta * c;
+    const double xa = 2.0 * beta * a, xc = 2.0 * beta * c;
+    ea[k] = xa;
+    ec[k] = xc;
+    ed[k] = -(xa + xc);
+    mm[k] = 1.0 + beta * (a + c);
+    cp[k] = k > k0 ? sk * (-beta * pc[k - 1]) : 0.0;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    // continuant chain; Q_{k-1} -> mm[k], Q_k -> cp[k] (same scale). A warp
+    // FP64 instruction costs the same with one active lane, so the chain
+    // holds only its own two operations per row; its inputs are loaded a
+    // batch of B rows ahead.
+    constexpr int B = 16;
+    double dA[B], gA[B], dB[B], gB[B];
+    auto load_batch = [&](int kb, double* dd, double* gg) {
 #pragma unroll
-    for (int q = 0; q < B; ++q) {
-      const int k = kb + q < k1 ? kb + q : k1 - 1;
-      av[q] = pa[k];
-      cv[q] = pc[k];
-    }
+      for (int q = 0; q < B; ++q) {
+        const int k = kb + q < k1 ? kb + q : k1 - 1;
+        dd[q] = mm[k];
+        gg[q] = cp[k];
+      }
+    };
+    load_batch(k0, dA, gA);
+    double q1 = 1.0, q2 = 0.0;
+    for (int kb = k0; kb < k1; kb += B) {
+      if (kb + B < k1) load_batch(kb + B, dB, gB);
 #pragma unroll
-    for (int q = 0; q < B; ++q) {
-      const int k = kb + q;
-      if (k < k1) {
-        const double s = -beta * av[q], up = -beta * cv[q], d = 1.0 + beta * (av[q] + cv[q]);
-        const double mk = 1.0 / (d - (k == k0 ? 0.0 : s * cprev));
-        cprev = up * mk;
-        sub[k] = s;
-        mm[k] = mk;
-        cp[k] = cprev;
-        sp[k] = up;
+      for (int q = 0; q < B; ++q) {
+        const int k = kb + q;
+        if (k < k1) {
+          if (((k - k0) & 7) == 0) {  // rescale q1, q2 by 2^-e, |q1| = f 2^e, f in [0.5, 1)
+            const long long bits = __double_as_longlong(q1);
+            const int e = (int)((bits >> 52) & 0x7ff) - 1022;
+            const double sc = __longlong_as_double((long long)(1023 - e) << 52);
+            q1 *= sc;
+            q2 *= sc;
+          }
+          const double qn = fma(dA[q], q1, -(gA[q] * q2));
+          mm[k] = q1;
+          cp[k] = qn;
+          q2 = q1;
+          q1 = qn;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        dA[q] = dB[q];
+        gA[q] = gB[q];
       }
     }
+  }
+  __syncwarp();
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const double mk = mm[k] / cp[k];
+    mm[k] = mk;
+    cp[k] = sp[k] * mk;
   }
 }
 
 cudaError_t cn_tables(afid_ctx* c, int l, double dt) {
   ProfScope ps(c, KF_CNTAB);
-  k_cn_tables<<<1, 32, 0, c->stream>>>(c->g, c->m, l, dt, c->scal, c->phys.nu, c->phys.kappa,
+  k_cn_tables<<<1, 96, 0, c->stream>>>(c->g, c->m, l, dt, c->scal, c->phys.nu, c->phys.kappa,
                                        c->cntab);
   c->launches++;
   return cudaGetLastError();
@@ -265,7 +370,7 @@ __global__ void k_cn_sweep(Grid g, const double* __restrict__ tab, double* R0, d
   if (col >= NXY) return;
   const int o = var < 2 ? 0 : (var == 2 ? 1 : 2);
   const int L = g.nz + 1;
-  const double* sub = tab + (size_t)o * 4 * L;
+  const double* sub = tab + (size_t)o * CN_TAB_ARRAYS * L;
   const double* mm = sub + L;
   const double* cp = mm + L;
   const double* sp = cp + L;

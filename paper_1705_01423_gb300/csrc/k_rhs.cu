@@ -7,11 +7,18 @@
 // fluxes; here every face flux is computed once and shared:
 //   * z: each thread owns one (x, y) column and walks k upwards, carrying the
 //     flux through face k+1 (cell k for w, T) to the next step in registers;
-//   * x: a warp spans 32 consecutive x; the neighbour's flux comes by shuffle;
+//   * x: a warp spans 32 consecutive x; the neighbour's flux comes by shuffle,
+//     across the two warps of a 64-wide block row through shared memory;
 //   * y: the block spans BY rows; fluxes of the neighbouring row come through a
 //     double-buffered shared-memory exchange (one barrier per k).
-// Constant factors (1/2, 1/4, 1/dx, dt gamma_l, ...) are folded, and the
-// Laplacian and wall-normal second differences use precomputed diagonals.
+// Only the block's outer edges recompute a neighbour's flux (every lane of
+// the edge warp issues that code, since masked lanes cost the same issue
+// slots), so wider blocks spend fewer operations on edges.
+// Constant factors (1/2, 1/4, 1/dx, dt gamma_l, ...) are folded; the
+// wall-normal term alpha_l dt d dzz q of R takes its three coefficients per
+// row from the substep's Crank-Nicolson table. The z-march of a column is
+// split into chunks (blockIdx.z) so that the grid balances over the SMs; a
+// chunk starts from the fluxes of the plane below it.
 // Same discretisation as the point-wise formulation it replaces:
 //   u: [(u_i+u_i+1)^2 - (u_i-1+u_i)^2]/(4dx) + [C_i,j+1 - C_i,j]/(4dy)
 //      + [Fz_k+1 - Fz_k]/(4 dzc_k), C_i,j = (v_i-1,j + v_i,j)(u_i,j-1 + u_i,j),
@@ -27,8 +34,11 @@ struct PhysR {
   double nu, kappa, buoy, ubot, utop;
 };
 
-template <bool HAS_T, int BY>
-__global__ void __launch_bounds__(32 * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR ph, int l, double dt_in,
+// WPR warps per block row: 1 (BX = min(32, nx), BY = 8) or 2 (BX = 64, BY = 4;
+// the two warps of a row pass their facing edge fluxes through shared
+// memory, so only the block's outer edges recompute neighbour fluxes).
+template <bool HAS_T, int BY, int WPR>
+__global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR ph, int l, double dt_in,
                                                     const double* __restrict__ scal,
                                                     const double* __restrict__ u,
                                                     const double* __restrict__ v,
@@ -38,8 +48,10 @@ __global__ void __launch_bounds__(32 * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR p
                                                     double* __restrict__ Hu, double* __restrict__ Hv,
                                                     double* __restrict__ Hw, double* __restrict__ HT,
                                                     double* __restrict__ Ru, double* __restrict__ Rv,
-                                                    double* __restrict__ Rw, double* __restrict__ RT) {
-  const int BX = blockDim.x;  // min(32, nx)
+                                                    double* __restrict__ Rw, double* __restrict__ RT,
+                                                    const double* __restrict__ cnt, int kchunk) {
+  const int BX = blockDim.x;  // min(32, nx) or 64
+  const int SW = WPR == 1 ? BX : 32;  // shuffle width: one block row per warp segment
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -51,32 +63,56 @@ __global__ void __launch_bounds__(32 * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR p
 
   const double dt = dt_in > 0.0 ? dt_in : scal[S_DT];
   const double cg = dt * rk_gamma(l), cr = dt * rk_rho(l), ca_ = dt * rk_alpha(l);
-  const double cnu = ca_ * ph.nu, ckap = ca_ * ph.kappa;
   const double cpx = ca_ * g.rdx, cpy = ca_ * g.rdy;
+  // alpha_l dt d dzz coefficients of this substep (k_cn_tables): cells (nu),
+  // faces (nu), faces (kappa); q_{k-1}, q_{k+1} and q_k weights
+  // (read as cnt[(set * CN_TAB_ARRAYS + 4..6) * L + k]; one base pointer keeps
+  // the register count down)
+  const int L = nz + 1;
+  // this block's range of k (the z-march is split into chunks for load balance)
+  const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
   const double qx = 0.25 * g.rdx, qy = 0.25 * g.rdy;  // 1/4 of the inverse spacings
   const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
   const double lap0 = 2.0 * (g.rdx2 + g.rdy2);
 
-  // shared y-exchange: [buffer][quantity][row][lane]
-  __shared__ double sx[2][4][BY][32];
+  // shared y-exchange: [buffer][quantity][row][x]; x-edge exchange between
+  // the two warps of a row: fxw, fxt of x = 32 and fxu of x = 31
+  __shared__ double sx[2][4][BY][32 * WPR];
+  __shared__ double sxe[2][3][BY];
 
   const size_t col = (size_t)j * nx + i;
   const size_t cim = (size_t)j * nx + im, cip = (size_t)j * nx + ip;
   const size_t cjm = (size_t)jm * nx + i, cjp = (size_t)jp * nx + i;
   const size_t cjpim = (size_t)jp * nx + im, cjmip = (size_t)jm * nx + ip;
 
-  // column values carried along k
-  double u0 = u[col], v0 = v[col];
-  double w0 = w[col], wk1 = w[NXY + col];
-  double t0 = HAS_T ? T[col] : 0.0, tk1 = HAS_T ? T[NXY + col] : 0.0;
-  double wim0 = w[cim], wjm0 = w[cjm];  // face k at (i-1), (j-1)
+  // column values carried along k (state at k = k0)
+  const size_t c0 = (size_t)k0 * NXY;
+  double u0 = u[c0 + col], v0 = v[c0 + col];
+  double w0 = w[c0 + col], wk1 = w[c0 + NXY + col];
+  double t0 = HAS_T ? T[c0 + col] : 0.0, tk1 = HAS_T ? T[c0 + NXY + col] : 0.0;
+  double wim0 = w[c0 + cim], wjm0 = w[c0 + cjm];  // face k at (i-1), (j-1)
   double fzu = 0.0, fzv = 0.0;          // u, v z-fluxes through face k (wall: 0)
   double fzw = 0.0, fzt = 0.0;          // w, T z-fluxes at cell k-1
   double ukm = ph.ubot, vkm = 0.0;      // u, v at k-1 (wall values at k = 0)
   double uipkm = 0.0, vjpkm = 0.0;      // u(i+1), v(j+1) at k-1
   double wkm = 0.0, tkm = 0.0, pkm = 0.0;
+  if (k0 > 0) {  // interior chunk start: the same quantities from plane k0 - 1
+    const size_t cm = c0 - NXY;
+    ukm = u[cm + col];
+    vkm = v[cm + col];
+    uipkm = u[cm + cip];
+    vjpkm = v[cm + cjp];
+    wkm = w[cm + col];
+    tkm = HAS_T ? T[cm + col] : 0.0;
+    pkm = p[cm + col];
+    fzu = (wim0 + w0) * (ukm + u0);
+    fzv = (wjm0 + w0) * (vkm + v0);
+    const double ws = wkm + w0;
+    fzw = ws * ws;
+    fzt = HAS_T ? ws * (tkm + t0) : 0.0;
+  }
 
-  for (int k = 0; k < nz; ++k) {
+  for (int k = k0; k < k1; ++k) {
     const size_t c = (size_t)k * NXY;
     const int buf = k & 1;
     // ---------------------------------------------------------------- loads at plane k
@@ -122,39 +158,65 @@ __global__ void __launch_bounds__(32 * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR p
     sx[buf][1][ty][tx] = fyv;
     sx[buf][2][ty][tx] = fyw;
     sx[buf][3][ty][tx] = fyt;
+    if (WPR == 2) {
+      if (tx == 32) {
+        sxe[buf][0][ty] = fxw;
+        sxe[buf][1][ty] = fxt;
+      }
+      if (tx == 31) sxe[buf][2][ty] = fxu;
+    }
     __syncthreads();
     // x neighbours by shuffle (lane i+1 / i-1 of the same row)
     const unsigned FULL = 0xffffffffu;
-    double Cip = __shfl_down_sync(FULL, C, 1, BX);
-    double fxum = __shfl_up_sync(FULL, fxu, 1, BX);
-    double fxw1 = __shfl_down_sync(FULL, fxw, 1, BX);
-    double fxt1 = __shfl_down_sync(FULL, fxt, 1, BX);
-    if (last_lane) {
-      Cip = (v0 + vip) * (u[c + cjmip] + uip);
-      if (k > 0) {
-        const double ufip = fma(m.wlo[k], uipkm, m.whi[k] * uip);
-        fxw1 = ufip * (w0 + wip);
-        if (HAS_T) fxt1 = ufip * (t0 + tip);
+    double Cip = __shfl_down_sync(FULL, C, 1, SW);
+    double fxum = __shfl_up_sync(FULL, fxu, 1, SW);
+    double fxw1 = __shfl_down_sync(FULL, fxw, 1, SW);
+    double fxt1 = __shfl_down_sync(FULL, fxt, 1, SW);
+    if (WPR == 2) {  // facing edges of the two warps of a row
+      if (tx == 31) {
+        Cip = sx[buf][0][ty][32];
+        fxw1 = sxe[buf][0][ty];
+        fxt1 = sxe[buf][1][ty];
+      }
+      if (tx == 32) fxum = sxe[buf][2][ty];
+    }
+    // Block-edge lanes recompute the neighbour's fluxes. The warp-uniform
+    // vote keeps these blocks a real branch taken only by the warps that
+    // hold an edge lane (if-converted, every warp would issue them).
+    if (__any_sync(FULL, last_lane)) {
+      if (last_lane) {
+        Cip = (v0 + vip) * (u[c + cjmip] + uip);
+        if (k > 0) {
+          const double ufip = fma(m.wlo[k], uipkm, m.whi[k] * uip);
+          fxw1 = ufip * (w0 + wip);
+          if (HAS_T) fxt1 = ufip * (t0 + tip);
+        }
       }
     }
-    if (first_lane) fxum = (uim + u0) * (uim + u0);
+    if (__any_sync(FULL, first_lane)) {
+      if (first_lane) fxum = (uim + u0) * (uim + u0);
+    }
     // y neighbours from shared memory (rows j+1 / j-1 of the block)
-    double Cjp, fyvm, fyw1, fyt1;
-    if (!last_row) {
-      Cjp = sx[buf][0][ty + 1][tx];
-      fyw1 = sx[buf][2][ty + 1][tx];
-      fyt1 = sx[buf][3][ty + 1][tx];
-    } else {
-      Cjp = (v[c + cjpim] + vjp) * (u0 + ujp);
-      fyw1 = 0.0;
-      fyt1 = 0.0;
-      if (k > 0) {
-        const double vfjp = fma(m.wlo[k], vjpkm, m.whi[k] * vjp);
-        fyw1 = vfjp * (w0 + wjp);
-        if (HAS_T) fyt1 = vfjp * (t0 + tjp);
+    const int typ = last_row ? ty : ty + 1, tym = first_row ? ty : ty - 1;
+    double Cjp = sx[buf][0][typ][tx];
+    double fyw1 = sx[buf][2][typ][tx];
+    double fyt1 = sx[buf][3][typ][tx];
+    double fyvm = sx[buf][1][tym][tx];
+    if (__any_sync(FULL, last_row)) {
+      if (last_row) {
+        Cjp = (v[c + cjpim] + vjp) * (u0 + ujp);
+        fyw1 = 0.0;
+        fyt1 = 0.0;
+        if (k > 0) {
+          const double vfjp = fma(m.wlo[k], vjpkm, m.whi[k] * vjp);
+          fyw1 = vfjp * (w0 + wjp);
+          if (HAS_T) fyt1 = vfjp * (t0 + tjp);
+        }
       }
     }
-    fyvm = !first_row ? sx[buf][1][ty - 1][tx] : (vjm + v0) * (vjm + v0);
+    if (__any_sync(FULL, first_row)) {
+      if (first_row) fyvm = (vjm + v0) * (vjm + v0);
+    }
 
     // ---------------------------------------------------------------- u, v at cell k
     const double rdzc = m.rdzc[k];
@@ -163,8 +225,8 @@ __global__ void __launch_bounds__(32 * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR p
       const double A = (fxu - fxum) * qx + (Cjp - C) * qy + (fzu1 - fzu) * qz;
       const double lap = fma(ujp + ujm, g.rdy2, (uip + uim) * g.rdx2) - lap0 * u0;
       const double H = fma(ph.nu, lap, -A);
-      const double dzz = fma(m.cc[k], ukp, m.ca[k] * ukm) - (m.cc[k] + m.ca[k]) * u0;
-      double r = fma(cg, H, fma(cnu, dzz, -cpx * (p0 - p[c + cim])));
+      const double z = fma(cnt[4 * L + k], ukm, fma(cnt[5 * L + k], ukp, fma(cnt[6 * L + k], u0, -cpx * (p0 - p[c + cim]))));
+      double r = fma(cg, H, z);
       if (l > 0) r = fma(cr, Hu[c + col], r);
       Hu[c + col] = H;
       Ru[c + col] = r;
@@ -173,8 +235,8 @@ __global__ void __launch_bounds__(32 * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR p
       const double A = (Cip - C) * qx + (fyv - fyvm) * qy + (fzv1 - fzv) * qz;
       const double lap = fma(vjp + vjm, g.rdy2, (vip + vim) * g.rdx2) - lap0 * v0;
       const double H = fma(ph.nu, lap, -A);
-      const double dzz = fma(m.cc[k], vkp, m.ca[k] * vkm) - (m.cc[k] + m.ca[k]) * v0;
-      double r = fma(cg, H, fma(cnu, dzz, -cpy * (p0 - p[c + cjm])));
+      const double z = fma(cnt[4 * L + k], vkm, fma(cnt[5 * L + k], vkp, fma(cnt[6 * L + k], v0, -cpy * (p0 - p[c + cjm]))));
+      double r = fma(cg, H, z);
       if (l > 0) r = fma(cr, Hv[c + col], r);
       Hv[c + col] = H;
       Rv[c + col] = r;
@@ -195,8 +257,8 @@ __global__ void __launch_bounds__(32 * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR p
         const double lap = fma(wjp + wjm0, g.rdy2, (wip + wim0) * g.rdx2) - lap0 * w0;
         double H = fma(ph.nu, lap, -A);
         if (HAS_T) H = fma(ph.buoy, t0, H);
-        const double dzz = fma(m.fc[k], wk1, m.fa[k] * wkm) - (m.fc[k] + m.fa[k]) * w0;
-        double r = fma(cg, H, fma(cnu, dzz, -ca_ * rdzf * (p0 - pkm)));
+        const double z = fma(cnt[(CN_TAB_ARRAYS + 4) * L + k], wkm, fma(cnt[(CN_TAB_ARRAYS + 5) * L + k], wk1, fma(cnt[(CN_TAB_ARRAYS + 6) * L + k], w0, -ca_ * rdzf * (p0 - pkm))));
+        double r = fma(cg, H, z);
         if (l > 0) r = fma(cr, Hw[c + col], r);
         Hw[c + col] = H;
         Rw[c + col] = r;
@@ -205,8 +267,8 @@ __global__ void __launch_bounds__(32 * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR p
         const double A = (fxt1 - fxt) * hx + (fyt1 - fyt) * hy + (fzt1 - fzt) * qzf;
         const double lap = fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2) - lap0 * t0;
         const double H = fma(ph.kappa, lap, -A);
-        const double dzz = fma(m.fc[k], tk1, m.fa[k] * tkm) - (m.fc[k] + m.fa[k]) * t0;
-        double r = fma(cg, H, ckap * dzz);
+        const double z = fma(cnt[(2 * CN_TAB_ARRAYS + 4) * L + k], tkm, fma(cnt[(2 * CN_TAB_ARRAYS + 5) * L + k], tk1, cnt[(2 * CN_TAB_ARRAYS + 6) * L + k] * t0));
+        double r = fma(cg, H, z);
         if (l > 0) r = fma(cr, HT[c + col], r);
         HT[c + col] = H;
         RT[c + col] = r;
@@ -242,16 +304,33 @@ cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const d
                          double* Hv, double* Hw, double* HT) {
   ProfScope ps(c, KF_RHS);
   const Grid& g = c->g;
-  constexpr int BY = 8;
-  const int bx = g.nx < 32 ? g.nx : 32;
-  dim3 blk(bx, BY), grd(g.nx / bx, g.ny / BY);
+  const bool wide = g.nx >= 64;
+  const int BY = wide ? 4 : 8;
+  const int bx = wide ? 64 : (g.nx < 32 ? g.nx : 32);
+  // split the z-march into chunks so that the grid is about eight waves of
+  // two resident blocks per SM (the chunk start re-reads one plane)
+  const long long bxy = (long long)(g.nx / bx) * (g.ny / BY);
+  const long long want = 16LL * c->num_sms;
+  int nch = (int)((want + bxy - 1) / bxy);
+  nch = nch < 1 ? 1 : nch;
+  const int max_ch = g.nz / 16 > 0 ? g.nz / 16 : 1;
+  nch = nch > max_ch ? max_ch : nch;
+  const int kchunk = (g.nz + nch - 1) / nch;
+  nch = (g.nz + kchunk - 1) / kchunk;
+  dim3 blk(bx, BY), grd(g.nx / bx, g.ny / BY, nch);
   PhysR ph{c->phys.nu, c->phys.kappa, c->phys.buoyancy, c->phys.u_bot, c->phys.u_top};
-  if (T)
-    k_rhs_zm<true, BY><<<grd, blk, 0, c->stream>>>(g, c->m, ph, l, dt, c->scal, u, v, w, T, p, Hu, Hv,
-                                                   Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3]);
-  else
-    k_rhs_zm<false, BY><<<grd, blk, 0, c->stream>>>(g, c->m, ph, l, dt, c->scal, u, v, w, T, p, Hu,
-                                                    Hv, Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3]);
+#define AFID_RHS(HT_, BY_, W_)                                                                     \
+  k_rhs_zm<HT_, BY_, W_><<<grd, blk, 0, c->stream>>>(g, c->m, ph, l, dt, c->scal, u, v, w, T, p, Hu, Hv, \
+                                                     Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3],         \
+                                                     c->cntab, kchunk)
+  if (T) {
+    if (wide) AFID_RHS(true, 4, 2);
+    else AFID_RHS(true, 8, 1);
+  } else {
+    if (wide) AFID_RHS(false, 4, 2);
+    else AFID_RHS(false, 8, 1);
+  }
+#undef AFID_RHS
   c->launches++;
   return cudaGetLastError();
 }

@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
       const double* vrp = v + ((size_t)k * g.ny + jp) * nx;
       const double* wr = w + (size_t)row * nx;
       const double* wrp = wr + (size_t)g.ny * nx;
-      const double rdzc = m.rdzc[k];
+      // the scale (1/s) folded into the three inverse spacings
+      const double sx = g.rdx * scale, sy = g.rdy * scale, sz = m.rdzc[k] * scale;
       for (int n = t; n < M; n += T) {
         const int i = 2 * n;
         const double2 uu = *reinterpret_cast<const double2*>(ur + i);
@@ -171,10 +172,8 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
         const double2 v1 = *reinterpret_cast<const double2*>(vrp + i);
         const double2 w0 = *reinterpret_cast<const double2*>(wr + i);
         const double2 w1 = *reinterpret_cast<const double2*>(wrp + i);
-        double d0 = (uu.y - uu.x) * g.rdx + (v1.x - v0.x) * g.rdy + (w1.x - w0.x) * rdzc;
-        double d1 = (u2 - uu.y) * g.rdx + (v1.y - v0.y) * g.rdy + (w1.y - w0.y) * rdzc;
-        d0 *= scale;
-        d1 *= scale;
+        const double d0 = fma(uu.y - uu.x, sx, fma(v1.x - v0.x, sy, (w1.x - w0.x) * sz));
+        const double d1 = fma(u2 - uu.y, sx, fma(v1.y - v0.y, sy, (w1.y - w0.y) * sz));
         if (want_stats) amax = fmax(amax, fmax(fabs(d0), fabs(d1)));
         buf[pad8(n)] = C{(R)d0, (R)d1};
       }
@@ -520,14 +519,35 @@ __global__ void __launch_bounds__(1024) k_fft_y(Grid g, typename cplx<R>::T* __r
 // mixed precision the low modes (lambda < lam_thr) are left to k_thomas_low.
 // Forward elimination and back substitution of one column (rows k = 0..nz-1,
 // pa[0] = 0), with the loads of the next U rows issued together so that the
-// memory latency is paid once per U rows rather than once per row (U = 8 in
-// FP32, which is bound by memory latency; 4 in FP64, bound by the FP64 pipe,
-// where more registers per thread would cost resident threads).
+// memory latency is paid once per U rows rather than once per row (FP32,
+// which is bound by memory latency; FP64 keeps the plain loop).
 template <typename R, typename C>
 __device__ __forceinline__ void thomas_column(C* __restrict__ col, const R* __restrict__ mt,
                                               const R* __restrict__ pa, const R* __restrict__ pc,
                                               int nz, size_t plane, size_t tplane) {
-  constexpr int U = sizeof(R) == 4 ? 8 : 4;
+  if constexpr (sizeof(R) == 8) {
+    // FP64: bound by the FP64 pipe; the plain loop keeps registers (and
+    // resident threads) for it
+    C dp = C{(R)0, (R)0};
+#pragma unroll 4
+    for (int k = 0; k < nz; ++k) {
+      const C d = col[k * plane];
+      const R mk = mt[k * tplane];
+      const R ak = pa[k];
+      dp = C{(d.x - ak * dp.x) * mk, (d.y - ak * dp.y) * mk};
+      col[k * plane] = dp;
+    }
+    C x = dp;
+#pragma unroll 4
+    for (int k = nz - 2; k >= 0; --k) {
+      const C e = col[k * plane];
+      const R cp = pc[k] * mt[k * tplane];
+      x = C{e.x - cp * x.x, e.y - cp * x.y};
+      col[k * plane] = x;
+    }
+    return;
+  }
+  constexpr int U = 8;
   C dv[U];
   R mv[U];
   C dp = C{(R)0, (R)0};
