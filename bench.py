@@ -40,6 +40,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # SM clock. The ALU roofline below counts FP64 operations, each add, multiply
 # or FMA once, against this issue rate.
 FP64_OPS_PEAK = 2 * 152 * 2.070e9 / 1e12          # 0.629 T FP64 ops/s
+# The mixed-precision solve is measured at the accuracy it is held to: a
+# relative error of 1e-10 against the FP64 solve (its stopping rule's target).
+MIXED_TOL = 1e-10
 
 
 def parse():
@@ -261,7 +264,7 @@ def run_poisson_only(args):
     del ctx
     torch.cuda.synchronize()
     out["poisson_fp64"] = {"ms": ms64, "grid_points_per_s": pts / (ms64 / 1e3), "families_ms": fam64}
-    mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=1e-12,
+    mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
                    refine_max_iter=6, poisson_only=True, tma=tma)
     phim = torch.empty_like(b)
     _, info = mctx.poisson_solve(b, phim, info=True)
@@ -272,8 +275,9 @@ def run_poisson_only(args):
     famm = {k: v[0] for k, v in mctx.profile_read().items() if v[1]}
     err = float((phim - phi64).norm() / phi64.norm())
     out["poisson_mixed"] = {"ms": msm, "grid_points_per_s": pts / (msm / 1e3), "iters": info["iters"],
-                            "rel_l2_vs_fp64_gpu": err, "err_estimate": info["err_estimate"],
-                            "speedup_vs_fp64": ms64 / msm, "families_ms": famm}
+                            "refine_tol": MIXED_TOL, "rel_l2_vs_fp64_gpu": err,
+                            "err_estimate": info["err_estimate"], "speedup_vs_fp64": ms64 / msm,
+                            "families_ms": famm}
     print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "tma_y": tma, "poisson": out}))
 
 
@@ -476,15 +480,15 @@ def side_measurements(ctx, w, dev, tma=True):
     ms64 = timed(lambda: ctx.poisson_solve(b, phi64), 5, stream)
     out = {"poisson_fp64": {"ms": ms64, "grid_points_per_s": pts / (ms64 / 1e3)}}
     try:
-        mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=1e-12,
+        mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
                        refine_max_iter=6, poisson_only=True, tma=tma)
         phim = torch.empty_like(b)
         _, info = mctx.poisson_solve(b, phim, info=True)
         msm = timed(lambda: mctx.poisson_solve(b, phim), 5, stream)
         err = float((phim - phi64).norm() / phi64.norm())
         out["poisson_mixed"] = {"ms": msm, "grid_points_per_s": pts / (msm / 1e3), "iters": info["iters"],
-                                "rel_l2_vs_fp64_gpu": err, "err_estimate": info["err_estimate"],
-                                "speedup_vs_fp64": ms64 / msm}
+                                "refine_tol": MIXED_TOL, "rel_l2_vs_fp64_gpu": err,
+                                "err_estimate": info["err_estimate"], "speedup_vs_fp64": ms64 / msm}
         mctx.profile(True)
         mctx.profile_read()
         mctx.poisson_solve(b, phim)

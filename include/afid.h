@@ -98,7 +98,8 @@ typedef struct {
   double max_div;          /* afid_project / substep: max |D u| after projection     */
   double err_estimate;     /* mixed: estimated relative error of phi (stopping rule:
                               ||d_k||^2/||d_{k-1}|| <= refine_tol ||phi||, d_k the
-                              k-th correction); FP64: 0                              */
+                              k-th correction, k >= 2, times 100 at k = 2, with
+                              ||phi|| ~ ||d_1||); FP64: 0                            */
 } afid_info;
 
 typedef struct afid_ctx afid_ctx;

@@ -45,6 +45,7 @@ enum Scalar {
   S_D1NORM2,       // mixed: ||d_1||^2 (the first correction, a proxy for ||phi||^2)
   S_PHIMEAN,       // mixed: weighted mean of phi after the last correction
   S_FAULT,         // 1.0 when a bounded wait inside a kernel gave up
+  S_PROJ_RS,       // 1 / S_PROJ_S (formed once where S_PROJ_S is set)
   S_COUNT = 20
 };
 

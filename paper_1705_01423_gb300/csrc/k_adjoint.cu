@@ -69,7 +69,7 @@ __global__ void k_adj_proj_post(Grid g, Metric m, double* __restrict__ gu, doubl
                                 double* __restrict__ gw, const double* __restrict__ psi,
                                 const double* __restrict__ scal) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-  const double rs = 1.0 / scal[S_PROJ_S];
+  const double rs = scal[S_PROJ_RS];
   const int im = (i - 1) & (g.nx - 1), jm = (j - 1) & (g.ny - 1);
   const size_t c = ix(g, k, j, i), NXY = (size_t)g.nx * g.ny;
   const double f = psi[c];

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  if (dev_s) scale = 1.0 / scal[S_PROJ_S];
+  if (dev_s) scale = scal[S_PROJ_RS];
   const int M = g.M, T = M / 8;
   const int lines = blockDim.x / T;
   const int line = threadIdx.x / T, t = threadIdx.x - line * T;
@@ -220,16 +220,20 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
 // Same line transform and unpacking as k_r2c_x.
 enum { R32_FIRST = 0, R32_RESID = 1 };
 
+// Block sum of one double per thread, valid on thread 0. The values go
+// through shared memory (red: blockDim.x doubles) and only warp 0 adds them:
+// on this part a warp FP64 instruction costs the same whatever its active
+// lanes, so a shuffle tree in every warp would cost each warp five adds.
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
-  if (lane == 0) red[wid] = v;
+  red[threadIdx.x] = v;
   __syncthreads();
   double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-  return t;  // valid on thread 0
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) t += red[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
 }
 
 template <int MODE>
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
                                                  const double* __restrict__ skip) {
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[16];
+  __shared__ double red[512];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int M = g.M, T = M / 8;
   const int lines = blockDim.x / T;
@@ -448,23 +452,10 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
   }
   if (MODE != 0) {
     // per-block ||delta||^2 and sum of dzc * phi (weighted mean of phi)
-    __shared__ double red[2][16];
-    double dd = (double)d2;
-    for (int o = 16; o > 0; o >>= 1) {
-      dd += __shfl_xor_sync(0xffffffffu, dd, o);
-      psum += __shfl_xor_sync(0xffffffffu, psum, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red[0][threadIdx.x >> 5] = dd;
-      red[1][threadIdx.x >> 5] = psum;
-    }
-    __syncthreads();
+    __shared__ double red[512];
+    const double a = block_sum_d(to_double(d2), red);
+    const double b = block_sum_d(psum, red);
     if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0;
-      for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
-        a += red[0][wi];
-        b += red[1][wi];
-      }
       part[2 * blockIdx.x] = a;
       part[2 * blockIdx.x + 1] = b;
     }

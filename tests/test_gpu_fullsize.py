@@ -210,3 +210,21 @@ def test_poisson2048_mixed_sampled_and_closed_form():
     print("poisson2048: sampled-mode error %.3e, closed-form error %.3e, iterations %d"
           % (err_sampled, err_closed, info["iters"]))
     assert err_closed < 1e-3
+
+
+@pytest.mark.parametrize("name", ["rb512", "couette1024"])
+def test_mixed_at_1e10_fullsize(name):
+    """The mixed solve at the accuracy it is held to (refine_tol = 1e-10), at
+    the workload sizes the bench times: within 1e-10 of the (pinned) FP64 solve."""
+    w = synth.workload(name)
+    g = ogrid(w)
+    b = gpu(synth.noise(g.cell_shape(), seed=21))
+    ctx64 = make_ctx(w, poisson_only=True)
+    ref = ctx64.poisson_solve(b)
+    del ctx64
+    ctxm = make_ctx(w, precision="mixed", refine_tol=1e-10, refine_max_iter=6, poisson_only=True)
+    phi, info = ctxm.poisson_solve(b, info=True)
+    assert info["status"] in (0, 5)
+    err = rel_l2(phi, ref)
+    print("%s mixed at 1e-10: error %.3e, estimate %.3e, iterations %d" % (name, err, info["err_estimate"], info["iters"]))
+    assert err < 1e-10, (err, info)
