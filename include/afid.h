@@ -97,9 +97,9 @@ typedef struct {
   double rhs_absmax;       /* max |rhs|                                              */
   double max_div;          /* afid_project / substep: max |D u| after projection     */
   double err_estimate;     /* mixed: estimated relative error of phi (stopping rule:
-                              ||d_k||^2/||d_{k-1}|| <= refine_tol ||phi||, d_k the
-                              k-th correction, k >= 2, times 100 at k = 2, with
-                              ||phi|| ~ ||d_1||); FP64: 0                            */
+                              ||d_k||^2/||d_{k-1}|| <= refine_tol ||phi|| for k >= 3,
+                              ||d_2|| <= refine_tol ||phi|| at k = 2, d_k the k-th
+                              correction, ||phi|| ~ ||d_1||); FP64: 0                */
 } afid_info;
 
 typedef struct afid_ctx afid_ctx;

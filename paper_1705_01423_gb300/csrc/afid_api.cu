@@ -91,7 +91,7 @@ void free_all(afid_ctx* c) {
   void* ps[] = {c->metric_buf, c->twx64, c->twy64, c->twx32, c->twy32, c->mtab64, c->mtab32,
                 c->lamx, c->lamy, c->spec, c->phi, c->bbuf, c->R[0], c->R[1], c->R[2],
                 c->R[3], c->cntab, c->pa32, c->pc32, c->lowslot, c->low_modes, c->low_scratch, c->scal,
-                c->part, c->part2, c->part3};
+                c->part, c->part2, c->part3, c->rres, c->dprev, c->cff};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -179,7 +179,7 @@ size_t afid_workspace_bytes(const afid_grid_desc* d) {
   const bool mixed = d->precision == AFID_MIXED;
   size_t b = spec_elems(d) * (mixed ? 8 : 16) + tab * 8 + (mixed ? tab * 4 : 0);
   b += n * 8;                                   // phi
-  if (mixed) b += n * 8;                        // kept rhs
+  if (mixed) b += n * 8 + n * 12;               // kept rhs, residual (two-float), last correction
   if (!(d->flags & AFID_POISSON_ONLY)) b += 2 * n * 8 + 2 * nf * 8;  // R buffers
   return b;
 }
@@ -312,6 +312,9 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   c->phi = A.get<double>(n);
   if (mixed) {
     c->bbuf = A.get<double>(n);
+    c->rres = A.get<float2>(n);
+    c->dprev = A.get<float>(n);
+    c->cff = A.get<float2>((size_t)3 * nz);
     c->pa32 = A.get<float>(nz);
     c->pc32 = A.get<float>(nz);
     c->lowslot = A.get<int>((size_t)ny * (M + 1));
@@ -360,6 +363,19 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     }
     up(c->pa32, pa32.data(), nz * sizeof(float));
     up(c->pc32, pc32.data(), nz * sizeof(float));
+    // two-float splits (head = nearest FP32, tail = FP32 of the remainder) of
+    // pa, pc, pdiag for the extended-precision residual update
+    std::vector<float2> cff((size_t)3 * nz);
+    auto split = [](double x) {
+      const float h = (float)x;
+      return make_float2(h, (float)(x - (double)h));
+    };
+    for (int k = 0; k < nz; ++k) {
+      cff[k] = split(pa[k]);
+      cff[nz + k] = split(pc[k]);
+      cff[2 * nz + k] = split(pdiag[k]);
+    }
+    up(c->cff, cff.data(), cff.size() * sizeof(float2));
     up(c->lowslot, lowslot.data(), lowslot.size() * sizeof(int));
     if (c->nlow) up(c->low_modes, low.data(), low.size() * sizeof(int2));
   }

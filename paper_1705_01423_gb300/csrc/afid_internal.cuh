@@ -135,6 +135,12 @@ struct afid_ctx {
   double* part2;  // mixed: per-block (||delta||^2, sum dzc delta) of the accumulate pass
   int part2_len;
   double* part3;  // mixed: per-block partials of the forward pass (stats of b / ||r||^2)
+  // mixed: the last residual as a two-float (head, tail) pair, the last FP32
+  // correction added to phi, and two-float splits of pa, pc, pdiag ([3][nz])
+  // for the residual update r_k = r_{k-1} - L delta_{k-1}
+  float2* rres;
+  float* dprev;
+  float2* cff;
   size_t bytes;
   long long launches;
   afid::Prof* prof;
@@ -162,11 +168,12 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
 int c2r_blocks(const Grid& g);
 // Mixed-precision refined solve of L phi = b (FP64 b, resident) into phi.
 cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi, bool stats);
-// One FP32 spectral solve of the refinement: b (first) or the FP64 residual
-// (b - mean) - L phi_in, formed in the forward transform; phi = delta (first)
-// or phi += delta - mean_W(phi).
+// One FP32 spectral solve of refinement step `it`: b (it = 0), the FP64
+// residual (b - mean) - L phi_in (it = 1) or the residual update
+// r - L delta_prev in two-float arithmetic (it >= 2), formed in the forward
+// transform; phi = delta (it = 0) or phi += delta - mean_W(phi).
 cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_in, double* phi,
-                                const double* skip, bool first, bool stats);
+                                const double* skip, int it, bool stats);
 // Reduction of the stats of b taken by the first forward transform.
 cudaError_t bstats_final(afid_ctx* c);
 // b = D(u, v, w) / s (s from S_PROJ_S)

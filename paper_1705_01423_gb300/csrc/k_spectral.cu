@@ -99,6 +99,47 @@ __device__ __forceinline__ void two_sum_acc(double& s, double& c, double x) {
   c = __dadd_rn(c, e);
 }
 
+// The part of x below its FP32 truncation to_real<float>(x), as an FP32
+// number (integer operations and one integer-to-float conversion: the 29
+// mantissa bits dropped by the truncation, scaled by 2^(e - 52), the scale a
+// subnormal FP32 power of two for small |x|). to_real<float>(x) + low_part(x)
+// equals x to about 2^-48 relative for |x| >= 2^-74, with gradually less
+// precision in the tail below that.
+__device__ __forceinline__ float low_part(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned lo29 = (unsigned)b & 0x1fffffffu;
+  const int e = (int)((b >> 52) & 0x7ff);       // biased FP64 exponent
+  const int fe = e - 1075 + 127;                // FP32 biased exponent of 2^(e - 1075)
+  if (fe <= -23 || fe >= 255 || lo29 == 0u) return 0.f;
+  const unsigned sb = fe > 0 ? (unsigned)fe << 23 : 1u << (fe + 22);
+  const float mag = __uint2float_rn(lo29) * __uint_as_float(sb);
+  return (b >> 63) ? -mag : mag;
+}
+
+// Two-float accumulation (sh, sl) += (ch + cl) v for an FP32 v: the product
+// ch v is split exactly into p + pe (FMA), p is added by TwoSum, and the
+// rounding errors with cl v and pe are collected in sl. Intrinsics keep every
+// step as written.
+__device__ __forceinline__ void ff_acc(float& sh, float& sl, float ch, float cl, float v) {
+  const float p = __fmul_rn(ch, v);
+  const float pe = __fmaf_rn(ch, v, -p);
+  const float t = __fadd_rn(sh, p);
+  const float tp = __fsub_rn(t, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, tp)), __fsub_rn(p, tp));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(e, __fmaf_rn(cl, v, pe)));
+}
+
+// (hi, lo) = a - b for two-float a, b, renormalised (|lo| <= ulp(hi)/2).
+__device__ __forceinline__ float2 ff_sub(float ah, float al, float bh, float bl) {
+  const float t = __fsub_rn(ah, bh);
+  const float tp = __fsub_rn(t, ah);
+  const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(t, tp)), __fsub_rn(-bh, tp));
+  const float lo = __fadd_rn(e, __fsub_rn(al, bl));
+  const float hi = __fadd_rn(t, lo);
+  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, t)));
+}
+
 // Product rounded on its own (never fused into a following add).
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
@@ -210,15 +251,25 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
 // --------------------------------------------------------------------------
 // Mixed precision forward x transform: FP64 input line -> FP32 spectrum, no
 // FP64 arithmetic per point except where the refinement needs it.
-//   R32_FIRST: line = b. FP64 per-block partial sums of dzc*b and b (and of
-//              b^2 and max |b| with stats) for the weighted mean removed from
-//              b (solvability) and the reported norm: part[3 blk + 0..2].
+//   R32_FIRST: line = b. Per-block partial sums of dzc*b and b (and of b^2
+//              and max |b| with stats) for the weighted mean removed from b
+//              (solvability) and the reported norm: part[3 blk + 0..2]. The
+//              row sums are compensated FP32 sums of the FP64 values split
+//              into head and tail (about 2^-46 relative), b^2 in FP32.
 //   R32_RESID: line = r = (b - mean_W b) - L phi, the refinement's FP64
 //              residual, computed on the fly (7-point operator of Sec. 2.2;
 //              8 FP64 operations per point); with stats the per-block ||r||^2
 //              (FP32, report only) in part[3 blk].
+//   R32_RESUPD: line = r_k = r_{k-1} - L delta_{k-1} (k >= 2), with
+//              r_{k-1} the stored two-float residual and delta_{k-1} the FP32
+//              correction the previous step added to phi; the 7-point sum in
+//              two-float arithmetic (no FP64 operations). The error of this
+//              update is a few 2^-46 of the stencil's terms, i.e. of
+//              |r_{k-1}| times the local condition, far below the FP32
+//              accuracy of the solve it feeds; r_k is stored back.
+// R32_RESID and R32_RESUPD store the residual as (head, tail) in rres.
 // Same line transform and unpacking as k_r2c_x.
-enum { R32_FIRST = 0, R32_RESID = 1 };
+enum { R32_FIRST = 0, R32_RESID = 1, R32_RESUPD = 2 };
 
 // Block sum of one double per thread, valid on thread 0. The values go
 // through shared memory (red: blockDim.x doubles) and only warp 0 adds them:
@@ -241,7 +292,9 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
                                                  const double* __restrict__ phi, float2* __restrict__ spec,
                                                  const float2* __restrict__ tw, double* __restrict__ scal,
                                                  double* __restrict__ part, int stats,
-                                                 const double* __restrict__ skip) {
+                                                 const double* __restrict__ skip, float2* __restrict__ rres,
+                                                 const float* __restrict__ dprev,
+                                                 const float2* __restrict__ cff) {
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[512];
@@ -256,7 +309,7 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
   float2* buf = sm + line * stride;
   float2* stw = sm + lines * stride;  // twiddle table, nx entries
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
-  double s_row = 0.0, s2 = 0.0;
+  float fs = 0.f, fc = 0.f, fs2 = 0.f;  // FIRST: compensated FP32 row sum, sum of squares
   float rr = 0.f;
   unsigned long long amax = 0ull;
   int k = 0;
@@ -268,17 +321,21 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
       const double2* s = reinterpret_cast<const double2*>(b + r0);
       for (int n = t; n < M; n += T) {
         const double2 x = s[n];
-        s_row += x.x + x.y;
+        const float hx = to_real<float>(x.x), hy = to_real<float>(x.y);
+        // row sum of b without FP64 arithmetic: TwoSum of the FP32 heads,
+        // the tails and the rounding errors collected in fc
+        two_sum_acc(fs, fc, hx);
+        two_sum_acc(fs, fc, hy);
+        fc = __fadd_rn(fc, __fadd_rn(low_part(x.x), low_part(x.y)));
         if (stats) {
-          s2 = fma(x.x, x.x, s2);
-          s2 = fma(x.y, x.y, s2);
+          fs2 = fmaf(hx, hx, fmaf(hy, hy, fs2));
           const unsigned long long ax = (unsigned long long)__double_as_longlong(x.x) & 0x7fffffffffffffffull;
           const unsigned long long ay = (unsigned long long)__double_as_longlong(x.y) & 0x7fffffffffffffffull;
           amax = max(amax, max(ax, ay));
         }
-        buf[pad8(n)] = make_float2(to_real<float>(x.x), to_real<float>(x.y));
+        buf[pad8(n)] = make_float2(hx, hy);
       }
-    } else {
+    } else if (MODE == R32_RESID) {
       const int j = row - k * g.ny;
       const size_t NXY = (size_t)nx * g.ny;
       const size_t rjp = ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * nx;
@@ -316,6 +373,52 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
         const float2 r32 = make_float2(to_real<float>(rx), to_real<float>(ry));
         if (stats) rr = fmaf(r32.x, r32.x, fmaf(r32.y, r32.y, rr));
         buf[pad8(n)] = r32;
+        reinterpret_cast<float4*>(rres + r0 + i)[0] = make_float4(r32.x, low_part(rx), r32.y, low_part(ry));
+      }
+    } else {  // R32_RESUPD
+      const int j = row - k * g.ny;
+      const size_t NXY = (size_t)nx * g.ny;
+      const size_t rjp = ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * nx;
+      const size_t rjm = ((size_t)k * g.ny + ((j - 1) & (g.ny - 1))) * nx;
+      const float2 ca = cff[k], cc = cff[g.nz + k], cd = cff[2 * g.nz + k];
+      const float xh = to_real<float>(g.rdx2), xl = low_part(g.rdx2);
+      const float yh = to_real<float>(g.rdy2), yl = low_part(g.rdy2);
+      const bool up = k < g.nz - 1, dn = k > 0;
+      for (int n = t; n < M; n += T) {
+        const int i = 2 * n;
+        const float2 f = *reinterpret_cast<const float2*>(dprev + r0 + i);
+        const float fw = dprev[r0 + ((i - 1) & (nx - 1))];
+        const float fe = dprev[r0 + ((i + 2) & (nx - 1))];
+        const float2 fn = *reinterpret_cast<const float2*>(dprev + rjp + i);
+        const float2 fs = *reinterpret_cast<const float2*>(dprev + rjm + i);
+        // S = L delta = rdx2 (w + e) + rdy2 (s + n) + pc up + pa down - pdiag centre
+        float sxh = 0.f, sxl = 0.f, syh = 0.f, syl = 0.f;
+        ff_acc(sxh, sxl, -cd.x, -cd.y, f.x);
+        ff_acc(syh, syl, -cd.x, -cd.y, f.y);
+        ff_acc(sxh, sxl, xh, xl, fw);
+        ff_acc(sxh, sxl, xh, xl, f.y);
+        ff_acc(syh, syl, xh, xl, f.x);
+        ff_acc(syh, syl, xh, xl, fe);
+        ff_acc(sxh, sxl, yh, yl, fn.x);
+        ff_acc(sxh, sxl, yh, yl, fs.x);
+        ff_acc(syh, syl, yh, yl, fn.y);
+        ff_acc(syh, syl, yh, yl, fs.y);
+        if (up) {
+          const float2 fu = *reinterpret_cast<const float2*>(dprev + r0 + NXY + i);
+          ff_acc(sxh, sxl, cc.x, cc.y, fu.x);
+          ff_acc(syh, syl, cc.x, cc.y, fu.y);
+        }
+        if (dn) {
+          const float2 fd = *reinterpret_cast<const float2*>(dprev + r0 - NXY + i);
+          ff_acc(sxh, sxl, ca.x, ca.y, fd.x);
+          ff_acc(syh, syl, ca.x, ca.y, fd.y);
+        }
+        const float4 ro = reinterpret_cast<const float4*>(rres + r0 + i)[0];
+        const float2 nx2 = ff_sub(ro.x, ro.y, sxh, sxl);
+        const float2 ny2 = ff_sub(ro.z, ro.w, syh, syl);
+        if (stats) rr = fmaf(nx2.x, nx2.x, fmaf(ny2.x, ny2.x, rr));
+        buf[pad8(n)] = make_float2(nx2.x, ny2.x);
+        reinterpret_cast<float4*>(rres + r0 + i)[0] = make_float4(nx2.x, nx2.y, ny2.x, ny2.y);
       }
     }
   }
@@ -339,10 +442,11 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
     }
   }
   if (MODE == R32_FIRST) {
+    const double s_row = to_double(fs) + to_double(fc);
     const double sw = active ? m.dzc[k] * s_row : 0.0;
     const double a = block_sum_d(sw, red);
     const double c = block_sum_d(s_row, red);
-    const double d = stats ? block_sum_d(s2, red) : 0.0;
+    const double d = stats ? block_sum_d(to_double(fs2), red) : 0.0;
     if (threadIdx.x == 0) {
       part[3 * blockIdx.x] = a;
       part[3 * blockIdx.x + 1] = c;
@@ -377,7 +481,8 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
                                                double scale, double* __restrict__ phi,
                                                const double* __restrict__ skip,
                                                double* __restrict__ part,
-                                               const double* __restrict__ pmean) {
+                                               const double* __restrict__ pmean,
+                                               float* __restrict__ dprev) {
   using C = typename cplx<R>::T;
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -432,12 +537,16 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
         const R dx = mul_rn(z.x, sc), dy = mul_rn(z.y, sc);
         d2 += dx * dx + dy * dy;
         if (MODE == 1) {        // later corrections are small: their sum in FP32
-          double2 r = make_double2(to_double(dx - pm), to_double(dy - pm));
+          const R ex = dx - pm, ey = dy - pm;
+          double2 r = make_double2(to_double(ex), to_double(ey));
           const double2 old = o2[n];
           r.x += old.x;
           r.y += old.y;
           o2[n] = r;
           dsum += dx + dy;
+          // the correction as added, for the next residual update
+          if (dprev) reinterpret_cast<typename cplx<R>::T*>(dprev + (size_t)row * g.nx)[n] =
+              typename cplx<R>::T{ex, ey};
         } else {                // the first correction is the bulk of phi:
           o2[n] = make_double2(to_double(dx), to_double(dy));
           // compensated FP32 sum: exact rounding error of every addition
@@ -978,7 +1087,8 @@ static cudaError_t run_c2r(afid_ctx* c, const typename cplx<R>::T* spec,
   const double scale = 1.0 / ((double)g.nx * (double)g.ny);
   auto kf = mode == 1 ? k_c2r_x<R, 1> : (mode == 2 ? k_c2r_x<R, 2> : k_c2r_x<R, 0>);
   cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, spec, tw, scale, phi, skip, part, c->scal + S_PHIMEAN);
+  kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, spec, tw, scale, phi, skip, part, c->scal + S_PHIMEAN,
+                                           sizeof(R) == sizeof(float) ? c->dprev : nullptr);
   c->launches++;
   return cudaGetLastError();
 }
@@ -1026,7 +1136,8 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
 // phi = delta (first) or phi += delta, with per-block partials of ||delta||^2
 // and of sum dzc phi in c->part2; every kernel returns at once when *skip != 0.
 cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_in, double* phi,
-                                const double* skip, bool first, bool stats) {
+                                const double* skip, int it, bool stats) {
+  const bool first = it == 0;
   const Grid& g = c->g;
   float2* spec = static_cast<float2*>(c->spec);
   cudaError_t e;
@@ -1035,10 +1146,10 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_
     const int T = g.M / 8, lines = r2c_lines<float>(g);
     const size_t sm = (size_t)lines * line_smem<float>(g.M) + (size_t)g.nx * sizeof(float2);
     const int blocks = ceil_div((long long)g.nz * g.ny, lines);
-    auto kf = first ? k_r2c_x32<R32_FIRST> : k_r2c_x32<R32_RESID>;
+    auto kf = it == 0 ? k_r2c_x32<R32_FIRST> : (it == 1 ? k_r2c_x32<R32_RESID> : k_r2c_x32<R32_RESUPD>);
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, b, phi_in, spec, c->twx32, c->scal, c->part3,
-                                             stats ? 1 : 0, skip);
+                                             stats ? 1 : 0, skip, c->rres, c->dprev, c->cff);
     c->launches++;
     if ((e = cudaGetLastError())) return e;
   }
