@@ -40,7 +40,8 @@ extern "C" {
 typedef enum {
   AFID_OK = 0,
   AFID_ERR_INVALID_ARG = 1,      /* NULL pointer, bad index, non-positive length ...      */
-  AFID_ERR_UNSUPPORTED_SIZE = 2, /* nx, ny not a power of two in [8, 4096]; nz < 3 or > 4096 */
+  AFID_ERR_UNSUPPORTED_SIZE = 2, /* nx, ny not of the form 2^a 3^b 5^c, nx not a multiple
+                                    of 16 or ny of 8, either > 4096; nz < 3 or > 4096   */
   AFID_ERR_ALIGNMENT = 3,        /* a device pointer not 16-byte aligned                  */
   AFID_ERR_NOT_CONVERGED = 4,    /* mixed refinement hit refine_max_iter (phi is the best) */
   AFID_ERR_INCONSISTENT_RHS = 5, /* |weighted mean of rhs| > 1e-8 max|rhs| (reported only
@@ -70,7 +71,9 @@ typedef enum {
                                one for the FP32 passes (FP64 always uses the plain one) */
 
 typedef struct {
-  int nx, ny, nz;          /* cells; nx, ny powers of two                            */
+  int nx, ny, nz;          /* cells; nx, ny = 2^a 3^b 5^c (the FFT radices 8/4/2/3/5),
+                              nx a multiple of 16, ny of 8 (the paper's grids, e.g.
+                              384, 768, 1280, are of this form)                     */
   double lx, ly;           /* periodic box lengths                                   */
   const double* zf;        /* HOST pointer, nz+1 face coordinates, strictly increasing */
   int precision;           /* afid_precision                                         */
@@ -211,7 +214,8 @@ const char* afid_kernel_family_name(int family);
  * AFID_NOALLOC_BYTES (16 MiB) that every GPU loading the library holds until
  * the process exits. The workspace needed is about
  *   16 nz ny roundup16(nx/2+1) + 8 nz (ny/2+1)(nx/2+1) bytes (+ small tables),
- * e.g. 64^3 or 128 x 128 x 64 fit; a grid that does not fit returns
+ * e.g. 64^3 or 128 x 128 x 64 fit; nx and ny must be powers of two here; a
+ * grid that does not fit or is not of that form returns
  * AFID_ERR_UNSUPPORTED_SIZE before anything is launched. The caller passes
  * the input rhs and the output phi (device, [nz][ny][nx], 16-byte aligned; they
  * may alias) and a cudaStream_t. The call uploads the tables from a static

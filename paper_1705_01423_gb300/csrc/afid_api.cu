@@ -12,11 +12,18 @@ using namespace afid;
 
 namespace {
 
-bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+// n = 2^a 3^b 5^c (the radices of the FFT passes)
+bool smooth235(int n) {
+  if (n <= 0) return false;
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
 
 afid_status validate_desc(const afid_grid_desc* d) {
   if (!d || !d->zf) return AFID_ERR_INVALID_ARG;
-  if (!pow2(d->nx) || !pow2(d->ny) || d->nx < 16 || d->ny < 8 || d->nx > 4096 || d->ny > 4096)
+  if (!smooth235(d->nx) || !smooth235(d->ny) || d->nx % 16 != 0 || d->ny % 8 != 0 || d->nx > 4096 ||
+      d->ny > 4096)
     return AFID_ERR_UNSUPPORTED_SIZE;
   if (d->nz < 3 || d->nz > 4096) return AFID_ERR_UNSUPPORTED_SIZE;
   if (!(d->lx > 0.0) || !(d->ly > 0.0)) return AFID_ERR_INVALID_ARG;
@@ -160,7 +167,9 @@ const char* afid_status_string(afid_status s) {
   switch (s) {
     case AFID_OK: return "ok";
     case AFID_ERR_INVALID_ARG: return "invalid argument";
-    case AFID_ERR_UNSUPPORTED_SIZE: return "unsupported grid size (nx, ny powers of two in [16|8, 4096], 3 <= nz <= 4096)";
+    case AFID_ERR_UNSUPPORTED_SIZE:
+      return "unsupported grid size (nx, ny of the form 2^a 3^b 5^c, nx a multiple of 16, ny of 8, "
+             "both <= 4096; 3 <= nz <= 4096)";
     case AFID_ERR_ALIGNMENT: return "device pointer not 16-byte aligned";
     case AFID_ERR_NOT_CONVERGED: return "mixed-precision refinement did not converge";
     case AFID_ERR_INCONSISTENT_RHS: return "right-hand side has a non-zero weighted mean (removed)";

@@ -234,6 +234,26 @@ struct ProfScope {
   }
 };
 
+// Periodic neighbours of index i in [0, n) (any n; the grid sizes are
+// 2^a 3^b 5^c).
+__host__ __device__ __forceinline__ int wrap_next(int i, int n) { return i + 1 < n ? i + 1 : 0; }
+__host__ __device__ __forceinline__ int wrap_prev(int i, int n) { return i > 0 ? i - 1 : n - 1; }
+// i + d for 0 <= i < n, |d| < n
+__host__ __device__ __forceinline__ int wrap_add(int i, int d, int n) {
+  const int j = i + d;
+  return j >= n ? j - n : (j < 0 ? j + n : j);
+}
+
+inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Largest block width in x among {128, 64, 32, 16} that divides nx and is
+// at most `cap` (nx is a multiple of 16).
+inline int x_block(int nx, int cap) {
+  for (int b = 128; b >= 16; b /= 2)
+    if (b <= cap && nx % b == 0) return b;
+  return 16;
+}
+
 // Ordered bit pattern of a non-negative double for atomicMax.
 __device__ __forceinline__ unsigned long long dbl_key(double v) {
   return (unsigned long long)__double_as_longlong(v);

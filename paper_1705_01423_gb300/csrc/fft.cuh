@@ -1,12 +1,13 @@
-// Shared-memory Stockham FFT building blocks (radix 8 / 4 / 2) for sm_103a.
+// Shared-memory Stockham FFT building blocks (radix 8 / 4 / 2 / 3 / 5) for sm_103a.
 //
-// One line of N = 2^n complex points lives in shared memory with one padding
+// One line of N = 2^a 3^b 5^c complex points (8 | N) lives in shared memory with one padding
 // slot every 8 elements (pad(m) = m + m/8), so that the stride-R writes of a
 // Stockham pass spread over the banks. Each thread owns 8 complex values per
-// pass: one radix-8 butterfly, two radix-4 or four radix-2 butterflies. A line
-// is transformed by N/8 threads; the pass sequence is radix 8 while at least
-// three factors of two remain, then one radix-4 or radix-2 pass (the first
-// pass needs no twiddles, so the large radix goes first).
+// pass: one radix-8 butterfly, two radix-4 or four radix-2 butterflies (up to
+// three radix-3 or two radix-5 butterflies). A line is transformed by N/8
+// threads; the pass sequence is radix 8 while at least three factors of two
+// remain, then one radix-4 or radix-2 pass, then the factors 3 and 5 (the
+// first pass needs no twiddles, so the large radix goes first).
 //
 // Twiddles come from a table tw[m] = exp(-2 pi i m / NT) of the table length
 // NT (a multiple of N), computed on the host in FP64; the transform of length
@@ -83,6 +84,48 @@ template <bool INV, typename C> __device__ __forceinline__ void dft8(C* a) {
   a[7] = C{fma(-o3.x, h, e3.x), fma(-o3.y, h, e3.y)};
 }
 
+// 3-point DFT: y0 = a0 + s, y1,2 = a0 - s/2 -/+ i (sqrt(3)/2) d (forward),
+// s = a1 + a2, d = a1 - a2; the inverse flips the sign of i.
+template <bool INV, typename C> __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
+  using R = decltype(a0.x);
+  const R c = (R)0.86602540378443864676;  // sqrt(3)/2
+  const C s = cadd(a1, a2), d = csub(a1, a2);
+  const C t = C{fma((R)-0.5, s.x, a0.x), fma((R)-0.5, s.y, a0.y)};
+  a0 = cadd(a0, s);
+  const C u = C{c * d.x, c * d.y};  // (sqrt(3)/2) d
+  // -i u = (u.y, -u.x), +i u = (-u.y, u.x)
+  if (!INV) {
+    a1 = C{t.x + u.y, t.y - u.x};
+    a2 = C{t.x - u.y, t.y + u.x};
+  } else {
+    a1 = C{t.x - u.y, t.y + u.x};
+    a2 = C{t.x + u.y, t.y - u.x};
+  }
+}
+
+// 5-point DFT with w = exp(-2 pi i/5): s1 = a1 + a4, d1 = a1 - a4, s2 = a2 + a3,
+// d2 = a2 - a3; t1 = a0 + c1 s1 + c2 s2, t2 = a0 + c2 s1 + c1 s2,
+// u1 = n1 d1 + n2 d2, u2 = n2 d1 - n1 d2 (c_m = cos(2 pi m/5), n_m = sin(2 pi m/5));
+// y1 = t1 - i u1, y4 = t1 + i u1, y2 = t2 - i u2, y3 = t2 + i u2 (forward; the
+// inverse flips the sign of i).
+template <bool INV, typename C> __device__ __forceinline__ void dft5(C* a) {
+  using R = decltype(a[0].x);
+  const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;
+  const R n1 = (R)0.95105651629515357212, n2 = (R)0.58778525229247312917;
+  const C s1 = cadd(a[1], a[4]), d1 = csub(a[1], a[4]);
+  const C s2 = cadd(a[2], a[3]), d2 = csub(a[2], a[3]);
+  const C t1 = C{fma(c2, s2.x, fma(c1, s1.x, a[0].x)), fma(c2, s2.y, fma(c1, s1.y, a[0].y))};
+  const C t2 = C{fma(c1, s2.x, fma(c2, s1.x, a[0].x)), fma(c1, s2.y, fma(c2, s1.y, a[0].y))};
+  const C u1 = C{fma(n2, d2.x, n1 * d1.x), fma(n2, d2.y, n1 * d1.y)};
+  const C u2 = C{fma(-n1, d2.x, n2 * d1.x), fma(-n1, d2.y, n2 * d1.y)};
+  a[0] = cadd(a[0], cadd(s1, s2));
+  const R sg = INV ? (R)-1 : (R)1;  // -i (forward) or +i (inverse) times u
+  a[1] = C{fma(sg, u1.y, t1.x), fma(-sg, u1.x, t1.y)};
+  a[4] = C{fma(-sg, u1.y, t1.x), fma(sg, u1.x, t1.y)};
+  a[2] = C{fma(sg, u2.y, t2.x), fma(-sg, u2.x, t2.y)};
+  a[3] = C{fma(-sg, u2.y, t2.x), fma(sg, u2.x, t2.y)};
+}
+
 // Shared-memory slot of point m of a line: padded line (one slot every 8
 // points), or column c of a tile of TK interleaved lines (point m of every
 // line in one row of TK slots, as a TMA box lands in shared memory).
@@ -94,46 +137,55 @@ template <int TK> struct ColIx {
   __device__ __forceinline__ int operator()(int m) const { return m * TK + c; }
 };
 
-// One Stockham pass of radix R on a shared-memory line `buf` of N points
-// (slot of point m: ix(m)), span p (size of the sub-transforms already done).
-// `t` in [0, N/8) is the thread's index within the line. All reads happen
-// before the barrier, all writes after it, so the pass is in place. The
-// caller guarantees that every thread of the block calls this (barriers inside).
+// One Stockham pass of radix R (8, 4, 2, 3 or 5) on a shared-memory line `buf`
+// of N points (slot of point m: ix(m)), span p (product of the radices of the
+// passes already done). `t` in [0, N/8) is the thread's index within the
+// line (8 | N); it takes butterflies j = t + b N/8 < N/R, b < ceil(8/R). All
+// reads happen before the barrier, all writes after it, so the pass is in
+// place. The caller guarantees that every thread of the block calls this
+// (barriers inside).
 template <int R, bool INV, typename C, typename IX>
 __device__ __forceinline__ void stockham_pass_ix(C* buf, int N, int p, const C* tw, int twstride,
                                                  int t, bool active, IX ix) {
-  constexpr int B = 8 / R;  // butterflies per thread
-  C x[8];
-  const int nb = N / R;
+  constexpr int B = (8 + R - 1) / R;  // butterflies per thread (at most)
+  C x[B * R];
+  const int nb = N / R, T = N / 8;
   if (active) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-      const int j = t + b * (N / 8);
+      const int j = t + b * T;
+      if ((8 % R == 0) || j < nb) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[b * R + r] = buf[ix(j + r * nb)];
+        for (int r = 0; r < R; ++r) x[b * R + r] = buf[ix(j + r * nb)];
+      }
     }
   }
   __syncthreads();
   if (active) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-      const int j = t + b * (N / 8);
-      const int k = j & (p - 1);
-      C* y = x + b * R;
-      if (p > 1) {
-        const int step = (N / (p * R)) * twstride;
+      const int j = t + b * T;
+      if ((8 % R == 0) || j < nb) {
+        // the radix-8/4/2 passes come first, so p is a power of two there
+        const int k = (8 % R == 0) ? (j & (p - 1)) : j % p;
+        C* y = x + b * R;
+        if (p > 1) {
+          const int step = (N / (p * R)) * twstride;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const C w = tw[r * k * step];
-          y[r] = INV ? cmulc(y[r], w) : cmul(y[r], w);
+          for (int r = 1; r < R; ++r) {
+            const C w = tw[r * k * step];
+            y[r] = INV ? cmulc(y[r], w) : cmul(y[r], w);
+          }
         }
-      }
-      if (R == 8) dft8<INV>(y);
-      if (R == 4) dft4<INV>(y[0], y[1], y[2], y[3]);
-      if (R == 2) dft2<INV>(y[0], y[1]);
-      const int o = (j - k) * R + k;
+        if (R == 8) dft8<INV>(y);
+        if (R == 4) dft4<INV>(y[0], y[1], y[2], y[3]);
+        if (R == 2) dft2<INV>(y[0], y[1]);
+        if (R == 3) dft3<INV>(y[0], y[1], y[2]);
+        if (R == 5) dft5<INV>(y);
+        const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[ix(o + r * p)] = y[r];
+        for (int r = 0; r < R; ++r) buf[ix(o + r * p)] = y[r];
+      }
     }
   }
   __syncthreads();
@@ -145,22 +197,47 @@ __device__ __forceinline__ void stockham_pass(C* buf, int N, int p, const C* tw,
   stockham_pass_ix<R, INV>(buf, N, p, tw, twstride, t, active, PadIx{});
 }
 
-// Full N-point transform of one line; N = 2^n, 8 <= N.
-template <bool INV, typename C, typename IX>
+// Full N-point transform of one line; N = 2^a 3^b 5^c with 8 | N. The
+// radix-8 passes go first (the first pass needs no twiddles), then one radix-4
+// or radix-2 pass for the rest of the power of two, then the radix-3 and
+// radix-5 passes.
+// GEN = false compiles the power-of-two passes only (N = 2^a): no radix-3/5
+// code, and so no registers held for it.
+template <bool INV, bool GEN, typename C, typename IX>
 __device__ __forceinline__ void fft_line_ix(C* buf, int N, const C* tw, int twstride, int t,
                                             bool active, IX ix) {
   int p = 1;
-  while (N / p >= 8) {
+  int n2 = N & -N;  // power-of-two part of N
+  int rest = N / n2;
+  while (n2 >= 8) {
     stockham_pass_ix<8, INV>(buf, N, p, tw, twstride, t, active, ix);
     p *= 8;
+    n2 /= 8;
   }
-  if (N / p == 4) stockham_pass_ix<4, INV>(buf, N, p, tw, twstride, t, active, ix);
-  else if (N / p == 2) stockham_pass_ix<2, INV>(buf, N, p, tw, twstride, t, active, ix);
+  if (n2 == 4) {
+    stockham_pass_ix<4, INV>(buf, N, p, tw, twstride, t, active, ix);
+    p *= 4;
+  } else if (n2 == 2) {
+    stockham_pass_ix<2, INV>(buf, N, p, tw, twstride, t, active, ix);
+    p *= 2;
+  }
+  if constexpr (GEN) {
+    while (rest % 3 == 0) {
+      stockham_pass_ix<3, INV>(buf, N, p, tw, twstride, t, active, ix);
+      p *= 3;
+      rest /= 3;
+    }
+    while (rest % 5 == 0) {
+      stockham_pass_ix<5, INV>(buf, N, p, tw, twstride, t, active, ix);
+      p *= 5;
+      rest /= 5;
+    }
+  }
 }
 
-template <bool INV, typename C>
+template <bool INV, bool GEN, typename C>
 __device__ __forceinline__ void fft_line(C* buf, int N, const C* tw, int twstride, int t, bool active) {
-  fft_line_ix<INV>(buf, N, tw, twstride, t, active, PadIx{});
+  fft_line_ix<INV, GEN>(buf, N, tw, twstride, t, active, PadIx{});
 }
 
 }  // namespace afid

@@ -18,7 +18,7 @@ __device__ __forceinline__ size_t ix(const Grid& g, int k, int j, int i) {
 }
 
 static inline dim3 pgrid(const Grid& g, int& bx) {
-  bx = g.nx < 128 ? g.nx : 128;
+  bx = x_block(g.nx, 128);
   return dim3(g.nx / bx, g.ny, g.nz);
 }
 
@@ -48,7 +48,7 @@ __global__ void k_adj_proj_pre(Grid g, Metric m, const double* __restrict__ gu,
                                double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   const double s = scal[S_PROJ_S], beta = scal[S_PROJ_BETA];
-  const int ip = (i + 1) & (g.nx - 1), jp = (j + 1) & (g.ny - 1);
+  const int ip = wrap_next(i, g.nx), jp = wrap_next(j, g.ny);
   const size_t c = ix(g, k, j, i), NXY = (size_t)g.nx * g.ny;
   const double rA = 1.0 / (g.dx * g.dy);
   const double rc = rA * m.rdzc[k];
@@ -70,7 +70,7 @@ __global__ void k_adj_proj_post(Grid g, Metric m, double* __restrict__ gu, doubl
                                 const double* __restrict__ scal) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   const double rs = scal[S_PROJ_RS];
-  const int im = (i - 1) & (g.nx - 1), jm = (j - 1) & (g.ny - 1);
+  const int im = wrap_prev(i, g.nx), jm = wrap_prev(j, g.ny);
   const size_t c = ix(g, k, j, i), NXY = (size_t)g.nx * g.ny;
   const double f = psi[c];
   gu[c] -= g.dy * m.dzc[k] * rs * (f - psi[ix(g, k, j, im)]);
@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(128) k_adj_explicit(Grid g, Metric m, PhysA ph
                                                       double* gv, double* gw, double* gT, double* gp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int ip = (i + 1) & (nx - 1), im = (i - 1) & (nx - 1);
-  const int jp = (j + 1) & (ny - 1), jm = (j - 1) & (ny - 1);
+  const int ip = wrap_next(i, nx), im = wrap_prev(i, nx);
+  const int jp = wrap_next(j, ny), jm = wrap_prev(j, ny);
   const size_t NXY = (size_t)nx * ny;
   const double da = dt * rk_alpha(l);
   const size_t c = ix(g, k, j, i);

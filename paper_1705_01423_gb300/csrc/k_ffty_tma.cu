@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(TileK<R>::MAXT, 1) k_fft_y_tma(const __grid_co
       break;
     }
     C* buf = tiles + (size_t)s * tile_elems;
-    fft_line_ix<INV>(buf, N, stw, 1, t, true, ColIx<TK>{c});
+    fft_line_ix<INV, false>(buf, N, stw, 1, t, true, ColIx<TK>{c});
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -144,12 +144,12 @@ static size_t ffty_tma_smem(const Grid& g, int stages) {
 }
 
 // Sets up the TMA y transform of a mixed-precision context when the sizes
-// allow it (16 <= ny <= 512, a tile ring of at least two stages in shared
+// allow it (ny a power of two, 16 <= ny <= 512, a tile ring of at least two stages in shared
 // memory); leaves c->tma_y = 0 (the plain kernel is used) otherwise.
 cudaError_t init_ffty_tma(afid_ctx* c) {
   c->tma_y = 0;
   const Grid& g = c->g;
-  if (g.ny > 512 || g.ny < 8) return cudaSuccess;
+  if (g.ny > 512 || g.ny < 8 || (g.ny & (g.ny - 1)) != 0) return cudaSuccess;  // power-of-two ny
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return cudaSuccess;
   if (c->prec != AFID_MIXED) return cudaSuccess;

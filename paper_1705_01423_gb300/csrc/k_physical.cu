@@ -42,7 +42,7 @@ __device__ double block_sum(double v) {
 }
 
 static inline dim3 point_grid(const Grid& g, int nzp, int& bx) {
-  bx = g.nx < 128 ? g.nx : 128;
+  bx = x_block(g.nx, 128);
   return dim3(g.nx / bx, g.ny, nzp);
 }
 
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) k_project(Grid g, Metric m, double* __res
   __syncthreads();
   const double sx = s * g.rdx, sy = s * g.rdy;
   const size_t NXY = (size_t)g.nx * g.ny;
-  const int im = (i - 1) & (g.nx - 1), jm = (j - 1) & (g.ny - 1);
+  const int im = wrap_prev(i, g.nx), jm = wrap_prev(j, g.ny);
   const size_t col = (size_t)j * g.nx + i, cim = (size_t)j * g.nx + im, cjm = (size_t)jm * g.nx + i;
   size_t c = (size_t)k0 * NXY;
   double f = phi[c + col];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_project(Grid g, Metric m, double* __res
 cudaError_t project(afid_ctx* c, double* u, double* v, double* w, double* p, const double* phi) {
   ProfScope ps(c, KF_PROJECT);
   const Grid& g = c->g;
-  const int bx = g.nx < 32 ? g.nx : 32, by = g.ny < 8 ? g.ny : 8;
+  const int bx = x_block(g.nx, 32), by = 8;
   // chunks of k so that the grid is several waves of resident blocks
   const long long bxy = (long long)(g.nx / bx) * (g.ny / by);
   const long long want = 32LL * c->num_sms;
@@ -146,7 +146,7 @@ __global__ void k_div(Grid g, Metric m, const double* __restrict__ u, const doub
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   const double rs = scal[S_PROJ_RS];
   const size_t c = at(g, k, j, i);
-  const int ip = (i + 1) & (g.nx - 1), jp = (j + 1) & (g.ny - 1);
+  const int ip = wrap_next(i, g.nx), jp = wrap_next(j, g.ny);
   const double d = (u[at(g, k, j, ip)] - u[c]) * g.rdx + (v[at(g, k, jp, i)] - v[c]) * g.rdy +
                    (w[c + (size_t)g.nx * g.ny] - w[c]) * m.rdzc[k];
   b[c] = d * rs;
@@ -170,10 +170,10 @@ __global__ void k_maxdiv(Grid g, Metric m, const double* __restrict__ u,
   // rows (k, j) across blocks, x across threads: no 64-bit division per point
   for (int row = blockIdx.x; row < g.nz * g.ny; row += gridDim.x) {
     const int k = row / g.ny, j = row - k * g.ny;
-    const int jp = (j + 1) & (g.ny - 1);
+    const int jp = wrap_next(j, g.ny);
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
       const size_t c = (size_t)row * g.nx + i;
-      const int ip = (i + 1) & (g.nx - 1);
+      const int ip = wrap_next(i, g.nx);
       const double d = (u[at(g, k, j, ip)] - u[c]) * g.rdx + (v[at(g, k, jp, i)] - v[c]) * g.rdy +
                        (w[c + (size_t)g.nx * g.ny] - w[c]) * m.rdzc[k];
       mx = fmax(mx, fabs(d));
@@ -202,11 +202,11 @@ __global__ void k_cfl(Grid g, Metric m, const double* __restrict__ u, const doub
   double mx = 0.0;
   for (int row = blockIdx.x; row < g.nz * g.ny; row += gridDim.x) {
     const int k = row / g.ny, j = row - k * g.ny;
-    const int jp = (j + 1) & (g.ny - 1);
+    const int jp = wrap_next(j, g.ny);
     const double rz = m.rdzc[k];
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
       const size_t c = (size_t)row * g.nx + i;
-      const int ip = (i + 1) & (g.nx - 1);
+      const int ip = wrap_next(i, g.nx);
       const double q = fabs(u[c] + u[at(g, k, j, ip)]) * g.rdx + fabs(v[c] + v[at(g, k, jp, i)]) * g.rdy +
                        fabs(w[c] + w[c + (size_t)g.nx * g.ny]) * rz;
       mx = fmax(mx, q);

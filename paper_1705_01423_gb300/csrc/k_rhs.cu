@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, P
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int ip = (i + 1) & (nx - 1), im = (i - 1) & (nx - 1);
-  const int jp = (j + 1) & (ny - 1), jm = (j - 1) & (ny - 1);
+  const int ip = wrap_next(i, nx), im = wrap_prev(i, nx);
+  const int jp = wrap_next(j, ny), jm = wrap_prev(j, ny);
   const size_t NXY = (size_t)nx * ny;
   const bool first_lane = tx == 0, last_lane = tx == BX - 1;
   const bool first_row = ty == 0, last_row = ty == BY - 1;
@@ -304,9 +304,9 @@ cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const d
                          double* Hv, double* Hw, double* HT) {
   ProfScope ps(c, KF_RHS);
   const Grid& g = c->g;
-  const bool wide = g.nx >= 64;
+  const bool wide = g.nx % 64 == 0;
   const int BY = wide ? 4 : 8;
-  const int bx = wide ? 64 : (g.nx < 32 ? g.nx : 32);
+  const int bx = wide ? 64 : x_block(g.nx, 32);
   // split the z-march into chunks so that the grid is about eight waves of
   // two resident blocks per SM (the chunk start re-reads one plane)
   const long long bxy = (long long)(g.nx / bx) * (g.ny / BY);

@@ -157,7 +157,7 @@ template <> __device__ __forceinline__ float to_real<float>(double x) {
   return __uint_as_float(sign | ((unsigned)e << 23) | mant);
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool GEN>
 __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* __restrict__ src,
                                                const double* __restrict__ u,
                                                const double* __restrict__ v,
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
       }
     } else {
       const int k = row / g.ny, j = row - (row / g.ny) * g.ny;
-      const int jp = (j + 1) & (g.ny - 1);
+      const int jp = wrap_next(j, g.ny);
       const double* ur = u + (size_t)row * nx;
       const double* vr = v + (size_t)row * nx;
       const double* vrp = v + ((size_t)k * g.ny + jp) * nx;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
       for (int n = t; n < M; n += T) {
         const int i = 2 * n;
         const double2 uu = *reinterpret_cast<const double2*>(ur + i);
-        const double u2 = ur[(i + 2) & (nx - 1)];
+        const double u2 = ur[wrap_add(i, 2, nx)];
         const double2 v0 = *reinterpret_cast<const double2*>(vr + i);
         const double2 v1 = *reinterpret_cast<const double2*>(vrp + i);
         const double2 w0 = *reinterpret_cast<const double2*>(wr + i);
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
     }
   }
   __syncthreads();
-  fft_line<false>(buf, M, stw, 2, t, active);
+  fft_line<false, GEN>(buf, M, stw, 2, t, active);
   if (active) {
     C* out = spec + (size_t)row * g.P;
     const R half = (R)0.5;
@@ -287,7 +287,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   return t;
 }
 
-template <int MODE>
+template <int MODE, bool GEN>
 __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double* __restrict__ b,
                                                  const double* __restrict__ phi, float2* __restrict__ spec,
                                                  const float2* __restrict__ tw, double* __restrict__ scal,
@@ -338,8 +338,8 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
     } else if (MODE == R32_RESID) {
       const int j = row - k * g.ny;
       const size_t NXY = (size_t)nx * g.ny;
-      const size_t rjp = ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * nx;
-      const size_t rjm = ((size_t)k * g.ny + ((j - 1) & (g.ny - 1))) * nx;
+      const size_t rjp = ((size_t)k * g.ny + (wrap_next(j, g.ny))) * nx;
+      const size_t rjm = ((size_t)k * g.ny + (wrap_prev(j, g.ny))) * nx;
       const double pc = m.pc[k], pa = m.pa[k], pd = m.pdiag[k];
       const double mean = scal[S_BMEAN];
       const double ax = -g.rdx2, ay = -g.rdy2;
@@ -347,8 +347,8 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
       for (int n = t; n < M; n += T) {
         const int i = 2 * n;
         const double2 f = *reinterpret_cast<const double2*>(phi + r0 + i);
-        const double fw = phi[r0 + ((i - 1) & (nx - 1))];
-        const double fe = phi[r0 + ((i + 2) & (nx - 1))];
+        const double fw = phi[r0 + (wrap_prev(i, nx))];
+        const double fe = phi[r0 + (wrap_add(i, 2, nx))];
         const double2 fn = *reinterpret_cast<const double2*>(phi + rjp + i);
         const double2 fs = *reinterpret_cast<const double2*>(phi + rjm + i);
         const double2 bb = *reinterpret_cast<const double2*>(b + r0 + i);
@@ -378,8 +378,8 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
     } else {  // R32_RESUPD
       const int j = row - k * g.ny;
       const size_t NXY = (size_t)nx * g.ny;
-      const size_t rjp = ((size_t)k * g.ny + ((j + 1) & (g.ny - 1))) * nx;
-      const size_t rjm = ((size_t)k * g.ny + ((j - 1) & (g.ny - 1))) * nx;
+      const size_t rjp = ((size_t)k * g.ny + (wrap_next(j, g.ny))) * nx;
+      const size_t rjm = ((size_t)k * g.ny + (wrap_prev(j, g.ny))) * nx;
       const float2 ca = cff[k], cc = cff[g.nz + k], cd = cff[2 * g.nz + k];
       const float xh = to_real<float>(g.rdx2), xl = low_part(g.rdx2);
       const float yh = to_real<float>(g.rdy2), yl = low_part(g.rdy2);
@@ -387,8 +387,8 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
       for (int n = t; n < M; n += T) {
         const int i = 2 * n;
         const float2 f = *reinterpret_cast<const float2*>(dprev + r0 + i);
-        const float fw = dprev[r0 + ((i - 1) & (nx - 1))];
-        const float fe = dprev[r0 + ((i + 2) & (nx - 1))];
+        const float fw = dprev[r0 + (wrap_prev(i, nx))];
+        const float fe = dprev[r0 + (wrap_add(i, 2, nx))];
         const float2 fn = *reinterpret_cast<const float2*>(dprev + rjp + i);
         const float2 fs = *reinterpret_cast<const float2*>(dprev + rjm + i);
         // S = L delta = rdx2 (w + e) + rdy2 (s + n) + pc up + pa down - pdiag centre
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
     }
   }
   __syncthreads();
-  fft_line<false>(buf, M, stw, 2, t, active);
+  fft_line<false, GEN>(buf, M, stw, 2, t, active);
   if (active) {
     float2* out = spec + (size_t)row * g.P;
     for (int q = t; q <= M / 2; q += T) {
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
 //   MODE 2 writes phi = delta (the first correction);
 //   MODE 1 adds phi += delta - mean_W(phi) (the mean measured after the
 //   previous correction), so that the gauge of phi is kept as it is refined.
-template <typename R, int MODE>
+template <typename R, int MODE, bool GEN>
 __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
                                                const typename cplx<R>::T* __restrict__ spec,
                                                const typename cplx<R>::T* __restrict__ tw,
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
     }
   }
   __syncthreads();
-  fft_line<true>(buf, M, stw, 2, t, active);
+  fft_line<true, GEN>(buf, M, stw, 2, t, active);
   R d2 = (R)0, dsum = (R)0, dcomp = (R)0;
   double psum = 0.0;
   if (active) {
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
 
 // --------------------------------------------------------------------------
 // Complex FFT along y for a tile of TK consecutive kx columns of one z plane.
-template <typename R, bool INV, int TK>
+template <typename R, bool INV, int TK, bool GEN>
 __global__ void __launch_bounds__(1024) k_fft_y(Grid g, typename cplx<R>::T* __restrict__ spec,
                                                 const typename cplx<R>::T* __restrict__ tw,
                                                 const double* __restrict__ skip) {
@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(1024) k_fft_y(Grid g, typename cplx<R>::T* __r
     if (c < ncol) sm[c * stride + pad8(ky)] = vals[q];
   }
   __syncthreads();
-  fft_line<INV>(sm + line * stride, Ny, stw, 1, t, line < ncol);
+  fft_line<INV, GEN>(sm + line * stride, Ny, stw, 1, t, line < ncol);
   for (int e = threadIdx.x; e < Ny * TK; e += blockDim.x) {
     const int ky = e / TK, c = e - (e / TK) * TK;
     if (c < ncol) base[(size_t)ky * g.P + c] = sm[c * stride + pad8(ky)];
@@ -1033,9 +1033,11 @@ static cudaError_t run_fft_y(afid_ctx* c, typename cplx<R>::T* spec, const typen
   dim3 grd(ceil_div(g.M + 1, tk), g.nz);
   const int thr = tk * (g.ny / 8);
   const size_t sm = (size_t)tk * ls + (size_t)g.ny * sizeof(typename cplx<R>::T);
+  const bool gen = !is_pow2(g.ny);  // radix-3/5 passes needed
 #define AFID_FFTY(TKV)                                                                        \
   do {                                                                                        \
-    auto kf = inv ? k_fft_y<R, true, TKV> : k_fft_y<R, false, TKV>;                          \
+    auto kf = inv ? (gen ? k_fft_y<R, true, TKV, true> : k_fft_y<R, true, TKV, false>)       \
+                  : (gen ? k_fft_y<R, false, TKV, true> : k_fft_y<R, false, TKV, false>);    \
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);           \
     kf<<<grd, thr, sm, c->stream>>>(g, spec, tw, skip);                                      \
   } while (0)
@@ -1060,13 +1062,14 @@ static cudaError_t run_r2c(afid_ctx* c, const double* rhs, const double* u, cons
   const int T = g.M / 8, lines = r2c_lines<R>(g);
   const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)g.nx * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
+  const bool gen = !is_pow2(g.M);
   if (rhs) {
-    auto kf = k_r2c_x<R, MODE_RHS>;
+    auto kf = gen ? k_r2c_x<R, MODE_RHS, true> : k_r2c_x<R, MODE_RHS, false>;
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, rhs, u, v, w, scale, spec, tw, c->scal,
                                              want_stats, skip, (int)dev_s);
   } else {
-    auto kf = k_r2c_x<R, MODE_DIV>;
+    auto kf = gen ? k_r2c_x<R, MODE_DIV, true> : k_r2c_x<R, MODE_DIV, false>;
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, rhs, u, v, w, scale, spec, tw, c->scal,
                                              want_stats, skip, (int)dev_s);
@@ -1085,7 +1088,9 @@ static cudaError_t run_c2r(afid_ctx* c, const typename cplx<R>::T* spec,
   const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)g.nx * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   const double scale = 1.0 / ((double)g.nx * (double)g.ny);
-  auto kf = mode == 1 ? k_c2r_x<R, 1> : (mode == 2 ? k_c2r_x<R, 2> : k_c2r_x<R, 0>);
+  const bool gen = !is_pow2(g.M);
+  auto kf = gen ? (mode == 1 ? k_c2r_x<R, 1, true> : (mode == 2 ? k_c2r_x<R, 2, true> : k_c2r_x<R, 0, true>))
+                : (mode == 1 ? k_c2r_x<R, 1, false> : (mode == 2 ? k_c2r_x<R, 2, false> : k_c2r_x<R, 0, false>));
   cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, spec, tw, scale, phi, skip, part, c->scal + S_PHIMEAN,
                                            sizeof(R) == sizeof(float) ? c->dprev : nullptr);
@@ -1146,7 +1151,11 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_
     const int T = g.M / 8, lines = r2c_lines<float>(g);
     const size_t sm = (size_t)lines * line_smem<float>(g.M) + (size_t)g.nx * sizeof(float2);
     const int blocks = ceil_div((long long)g.nz * g.ny, lines);
-    auto kf = it == 0 ? k_r2c_x32<R32_FIRST> : (it == 1 ? k_r2c_x32<R32_RESID> : k_r2c_x32<R32_RESUPD>);
+    const bool gen = !is_pow2(g.M);
+    auto kf = gen ? (it == 0 ? k_r2c_x32<R32_FIRST, true>
+                             : (it == 1 ? k_r2c_x32<R32_RESID, true> : k_r2c_x32<R32_RESUPD, true>))
+                  : (it == 0 ? k_r2c_x32<R32_FIRST, false>
+                             : (it == 1 ? k_r2c_x32<R32_RESID, false> : k_r2c_x32<R32_RESUPD, false>));
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, b, phi_in, spec, c->twx32, c->scal, c->part3,
                                              stats ? 1 : 0, skip, c->rres, c->dprev, c->cff);

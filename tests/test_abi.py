@@ -49,7 +49,8 @@ def desc(nx=32, ny=16, nz=8, zf=None, prec=0):
 
 
 @pytest.mark.parametrize("nx,ny,nz,code", [(24, 16, 8, 2), (32, 12, 8, 2), (8, 16, 8, 2), (32, 16, 2, 2),
-                                            (8192, 16, 8, 2), (32, 4, 8, 2)])
+                                            (8192, 16, 8, 2), (32, 4, 8, 2), (112, 16, 8, 2),
+                                            (96, 56, 8, 2), (16 * 11, 48, 8, 2), (4800, 48, 8, 2)])
 def test_create_rejects_unsupported_sizes(L, nx, ny, nz, code):
     from paper_1705_01423_gb300 import afid
     d, z = desc(nx, ny, nz, zf=np.linspace(0, 1, nz + 1))
@@ -57,6 +58,14 @@ def test_create_rejects_unsupported_sizes(L, nx, ny, nz, code):
     assert L.afid_create(C.byref(d), None, None, C.byref(h)) == code
     assert not h.value
     assert L.afid_workspace_bytes(C.byref(d)) == 0
+
+
+@pytest.mark.parametrize("nx,ny", [(96, 48), (160, 40), (384, 24), (1280, 1024), (768, 768), (48, 120)])
+def test_sizes_with_factors_3_and_5_accepted(L, nx, ny):
+    """nx, ny of the form 2^a 3^b 5^c (nx a multiple of 16, ny of 8) -- the
+    paper's Table 3/4 grids among them -- pass validation (host only)."""
+    d, z = desc(nx, ny, 8)
+    assert L.afid_workspace_bytes(C.byref(d)) > 0
 
 
 def test_create_rejects_bad_faces_and_precision(L):

@@ -289,3 +289,54 @@ def test_tma_y_transform_matches_plain_kernel(shape):
     assert rel_l2(a, p) < 1e-11
     ref = poisson.solve(g, cpu(b))
     assert rel_l2(a, ref) < TOLMIX
+
+
+RADIX35 = [(96, 48, 9), (160, 40, 7), (48, 120, 11), (384, 24, 5), (240, 24, 6)]
+
+
+@pytest.mark.parametrize("shape", RADIX35)
+def test_poisson_fp64_radix_3_and_5(shape):
+    """Sizes with factors 3 and 5 (radix-3 and radix-5 Stockham passes after the
+    radix-8/4/2 ones; nx/2 and ny both mixed-radix): FP64 solve against the
+    oracle within 1e-12."""
+    nx, ny, nz = shape
+    w = synth.workload("pc64", nx=nx, ny=ny, nz=nz, lx=1.7, ly=0.9)
+    g = ogrid(w)
+    b = synth.noise(g.cell_shape(), seed=nx + 3 * ny)
+    ref = poisson.solve(g, cpu(b))
+    phi = make_ctx(w, poisson_only=True).poisson_solve(gpu(b))
+    assert rel_l2(phi, ref) < TOL64
+
+
+@pytest.mark.parametrize("shape", [(96, 48, 9), (160, 40, 7)])
+def test_mixed_poisson_radix_3_and_5(shape):
+    nx, ny, nz = shape
+    w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
+    g = ogrid(w)
+    b = synth.noise(g.cell_shape(), seed=nx + ny + 1)
+    ref = poisson.solve(g, cpu(b))
+    phi, info = make_ctx(w, precision="mixed", refine_tol=1e-10, refine_max_iter=8,
+                         poisson_only=True).poisson_solve(gpu(b), info=True)
+    assert rel_l2(phi, ref) < TOLMIX, info
+
+
+@pytest.mark.parametrize("shape", [(96, 40, 12), (80, 24, 7)])
+def test_rk3_step_rb_radix_3_and_5(shape):
+    """Two full RK3 steps (explicit terms with periodic wraps at nx, ny not
+    powers of two, 32- and 16-wide blocks) against the oracle."""
+    nx, ny, nz = shape
+    w = synth.workload("rb512", nx=nx, ny=ny, nz=nz)
+    w.nu, w.kappa = 2e-3, 2e-3
+    g = ogrid(w)
+    ph = ts.Phys(nu=w.nu, kappa=w.kappa, buoyancy=1.0, T_bot=1.0, T_top=0.0)
+    st = rb_state(w, 2)
+    ref_state = tuple(cpu(a) for a in st)
+    ctx = make_ctx(w)
+    S = [gpu(a) for a in st]
+    H = [torch.zeros_like(S[0]), torch.zeros_like(S[1]), torch.zeros_like(S[2]), torch.zeros_like(S[3])]
+    Href = None
+    for step in range(2):
+        for l in range(3):
+            ref_state, Href = ts.substep(g, ph, l, 1e-2, ref_state, Href)
+            ctx.rk3_substep(l, 1e-2, *S, *H)
+    compare_state(S, ref_state, TOL64)

@@ -228,3 +228,30 @@ def test_mixed_at_1e10_fullsize(name):
     err = rel_l2(phi, ref)
     print("%s mixed at 1e-10: error %.3e, estimate %.3e, iterations %d" % (name, err, info["err_estimate"], info["iters"]))
     assert err < 1e-10, (err, info)
+
+
+def test_paper_table3_grid_384_substep():
+    """The paper's Table 3 grid 384 x 384 x 256 (radix-3 transforms in x and y):
+    one Rayleigh-Benard RK3 substep element by element against the oracle."""
+    w = synth.workload("rb512", nx=384, ny=384, nz=256)
+    ph = ts.Phys(nu=w.nu, kappa=w.kappa, buoyancy=1.0, T_bot=1.0, T_top=0.0)
+    substep_parity(w, perturbed_rb(w, 3), ph, 0, 2e-3)
+
+
+def test_paper_table4_grid_1280_poisson_sampled_modes():
+    """The paper's Table 4 Couette grid 1280 x 1024 x 256 (radix-5 transforms in
+    x): 16 sampled (kx, ky) columns of the FP64 solve against the sampled-mode
+    oracle within 1e-12."""
+    w = synth.workload("couette1024", nx=1280, ny=1024, nz=256)
+    g = ogrid(w)
+    b = synth.noise(g.cell_shape(), seed=77)
+    ctx = make_ctx(w, poisson_only=True)
+    B = gpu(b)
+    phi = ctx.poisson_solve(B)
+    assert residual_fp64(ctx, g, B, phi) < 1e-13
+    pairs = sampled.default_pairs(g, seed=3, count=16)
+    ref = sampled.solve_modes(g, b, pairs)
+    got = sampled.mode_columns(g, phi, pairs)
+    num = sum(np.linalg.norm(got[p] - ref[p]) ** 2 for p in pairs)
+    den = sum(np.linalg.norm(ref[p]) ** 2 for p in pairs)
+    assert np.sqrt(num / den) < 1e-12
