@@ -18,6 +18,10 @@ computes (AFiD, arXiv 1705.01423), written in PyTorch CPU float64 ops:
                Nusselt number (Sec. 2.1, Sec. 2.2 last paragraph)
   adjoint.py   reverse-mode derivatives of the above by automatic
                differentiation of the very same forward code
+  stats.py     wall-normal statistics: horizontal means per plane, Nusselt
+               numbers, wall shear stress, friction Reynolds number (Sec. 3.2,
+               Sec. 4)
+  sampled.py   the Poisson solve at a few wavenumber pairs (large grids)
 
 Coordinates follow the workloads, not the paper: x and y are the periodic,
 uniform directions and z is the bounded, stretched wall-normal direction (the
