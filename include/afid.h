@@ -160,6 +160,34 @@ afid_status afid_rk3_substep(afid_ctx* ctx, int l, double dt, double* u, double*
 afid_status afid_max_divergence(afid_ctx* ctx, const double* u, const double* v, const double* w,
                                 double* out_dev);
 
+/* Wall-normal statistics (the statistics of Sec. 3.2, accumulated only along
+ * the wall-normal direction; the Nusselt number of Sec. 4 and the friction
+ * velocity / friction Reynolds number of Sec. 4, Table 4).
+ * profiles (HOST, may be NULL): [nz+1][AFID_STAT_NQ] horizontal means,
+ *   0 <u>  1 <v>  2 <u^2>  3 <v^2>            on cell planes k = 0..nz-1 (row nz: 0)
+ *   4 <w>  5 <w^2>  6 <T>  7 <T^2>  8 <w T>   on face planes k = 0..nz (6-8: 0 without T)
+ * out (HOST, may be NULL): the scalars below, with H = zf[nz] - zf[0], Delta T =
+ * T_bot - T_top and h = H/2 from the context's afid_phys:
+ *   nu_volume  1 + <w T>_V / kappa (kappa = 1/sqrt(Ra Pr): Nu = 1 + sqrt(Ra Pr)<w T>_V),
+ *              <.>_V over interior faces weighted by dzf;
+ *   nu_bottom  -(<T>_1 - <T>_0) / dzc_0 / Delta T, nu_top likewise at the top wall
+ *              (conductive flux through the wall cells);
+ *   tau_bottom nu (<u>_0 - u_bot) / (dzc_0 / 2), tau_top nu (u_top - <u>_{nz-1}) /
+ *              (dzc_{nz-1} / 2) (wall value half a cell away, as in the viscous term);
+ *   re_tau     h u_tau / nu, u_tau = sqrt((|tau_bottom| + |tau_top|) / 2);
+ *   ke         <(u^2 + v^2 + w^2) / 2>_V (u, v weighted by dzc, w by dzf).
+ * u, v, w, T: device fields as in afid_rk3_substep (T may be NULL). The sums are
+ * FP64 in a fixed order (deterministic). The call synchronises the context's
+ * stream. */
+#define AFID_STAT_NQ 9
+typedef struct {
+  double nu_volume, nu_bottom, nu_top;
+  double tau_bottom, tau_top, re_tau;
+  double ke;
+} afid_stats;
+afid_status afid_statistics(afid_ctx* ctx, const double* u, const double* v, const double* w,
+                            const double* T, double* profiles, afid_stats* out);
+
 /* Transpose of the linear map rhs -> phi of afid_poisson_solve (exact
  * transpose: grhs = W_c solve(W_c^-1 gphi), W_c the cell volumes). gphi and
  * grhs: device [nz][ny][nx]; may alias. Always FP64. */

@@ -77,6 +77,7 @@ _SIGS = {
     "afid_cfl": (I, [P, P, P, P, D, D, P]),
     "afid_rk3_substep": (I, [P, I, D, P, P, P, P, P, P, P, P, P, C.POINTER(Info)]),
     "afid_max_divergence": (I, [P, P, P, P, P]),
+    "afid_statistics": (I, [P, P, P, P, P, P, P]),
     "afid_poisson_solve_adjoint": (I, [P, P, P]),
     "afid_project_adjoint": (I, [P, P, P, P, P, D, D]),
     "afid_rk3_substep_adjoint": (I, [P, I, D, P, P, P, P, P, P, P, P, P, P, P, P, P]),
@@ -145,6 +146,15 @@ class Physics:
     u_top: float = 0.0
     T_bot: float = 0.0
     T_top: float = 0.0
+
+
+STAT_NQ = 9
+
+
+class Stats(C.Structure):
+    _fields_ = [("nu_volume", C.c_double), ("nu_bottom", C.c_double), ("nu_top", C.c_double),
+                ("tau_bottom", C.c_double), ("tau_top", C.c_double), ("re_tau", C.c_double),
+                ("ke", C.c_double)]
 
 
 class Context:
@@ -261,6 +271,20 @@ class Context:
                                          _ptr(w, self.face, "w"), C.c_void_p(out.data_ptr())),
                "afid_max_divergence")
         return out
+
+    def statistics(self, u, v, w, T=None):
+        """Wall-normal statistics (afid_statistics): returns (profiles, scalars),
+        profiles a [nz+1][9] numpy array of horizontal means (<u>, <v>, <u^2>,
+        <v^2> on cell planes; <w>, <w^2>, <T>, <T^2>, <w T> on face planes) and
+        scalars a dict (nu_volume, nu_bottom, nu_top, tau_bottom, tau_top,
+        re_tau, ke)."""
+        prof = np.zeros((self.nz + 1, STAT_NQ), dtype=np.float64)
+        st = Stats()
+        _check(lib().afid_statistics(self._h, _ptr(u, self.cell, "u"), _ptr(v, self.cell, "v"),
+                                     _ptr(w, self.face, "w"),
+                                     _ptr(T, self.face, "T") if T is not None else None,
+                                     prof.ctypes.data_as(C.c_void_p), C.byref(st)), "afid_statistics")
+        return prof, {name: getattr(st, name) for name, _ in Stats._fields_}
 
     def rk3_substep(self, l, dt, u, v, w, T, p, Hu, Hv, Hw, HT, info=False):
         """dt <= 0 uses the dt set by the last cfl() call (device resident)."""

@@ -98,7 +98,7 @@ void free_all(afid_ctx* c) {
   void* ps[] = {c->metric_buf, c->twx64, c->twy64, c->twx32, c->twy32, c->mtab64, c->mtab32,
                 c->lamx, c->lamy, c->spec, c->phi, c->bbuf, c->R[0], c->R[1], c->R[2],
                 c->R[3], c->cntab, c->pa32, c->pc32, c->lowslot, c->low_modes, c->low_scratch, c->scal,
-                c->part, c->part2, c->part3, c->rres, c->dprev, c->cff};
+                c->part, c->part2, c->part3, c->rres, c->dprev, c->cff, c->stat_buf};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -337,6 +337,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   }
   c->cntab = A.get<double>((size_t)3 * CN_TAB_ARRAYS * (nz + 1));
   c->scal = A.get<double>(S_COUNT);
+  c->stat_buf = A.get<double>((size_t)(nz + 1) * AFID_STAT_NQ + 8);
   c->part_len = c->num_sms * 8;
   c->part = A.get<double>((size_t)3 * c->part_len);
   if (mixed) {
@@ -534,6 +535,33 @@ afid_status afid_rk3_substep(afid_ctx* c, int l, double dt, double* u, double* v
     return fill_info(c, info, c->prec == AFID_MIXED, true);
   }
   return cudaGetLastError() == cudaSuccess ? AFID_OK : AFID_ERR_CUDA;
+}
+
+afid_status afid_statistics(afid_ctx* c, const double* u, const double* v, const double* w,
+                            const double* T, double* profiles, afid_stats* out) {
+  if (!c) return AFID_ERR_INVALID_ARG;
+  afid_status st = check_fields({u, v, w});
+  if (st) return st;
+  if (T && (st = check_fields({T}))) return st;
+  if (statistics(c, u, v, w, T)) return AFID_ERR_CUDA;
+  const size_t np = (size_t)(c->g.nz + 1) * AFID_STAT_NQ;
+  double sc[8];
+  if (profiles &&
+      cudaMemcpyAsync(profiles, c->stat_buf, np * sizeof(double), cudaMemcpyDeviceToHost, c->stream))
+    return AFID_ERR_CUDA;
+  if (cudaMemcpyAsync(sc, c->stat_buf + np, sizeof(sc), cudaMemcpyDeviceToHost, c->stream))
+    return AFID_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream)) return AFID_ERR_CUDA;
+  if (out) {
+    out->nu_volume = sc[0];
+    out->nu_bottom = sc[1];
+    out->nu_top = sc[2];
+    out->tau_bottom = sc[3];
+    out->tau_top = sc[4];
+    out->re_tau = sc[5];
+    out->ke = sc[6];
+  }
+  return AFID_OK;
 }
 
 afid_status afid_poisson_solve_adjoint(afid_ctx* c, const double* gphi, double* grhs) {

@@ -141,6 +141,8 @@ struct afid_ctx {
   float2* rres;
   float* dprev;
   float2* cff;
+  // wall-normal statistics: profiles [nz+1][AFID_STAT_NQ] and 8 scalars
+  double* stat_buf;
   size_t bytes;
   long long launches;
   afid::Prof* prof;
@@ -176,6 +178,9 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_
                                 const double* skip, int it, bool stats);
 // Reduction of the stats of b taken by the first forward transform.
 cudaError_t bstats_final(afid_ctx* c);
+// Wall-normal statistics of (u, v, w, T) into c->stat_buf (profiles, then the
+// scalars of afid_stats).
+cudaError_t statistics(afid_ctx* c, const double* u, const double* v, const double* w, const double* T);
 // b = D(u, v, w) / s (s from S_PROJ_S)
 cudaError_t divergence_to(afid_ctx* c, const double* u, const double* v, const double* w, double* b);
 // projection with s, beta read from S_PROJ_S / S_PROJ_BETA
@@ -252,6 +257,17 @@ inline int x_block(int nx, int cap) {
   for (int b = 128; b >= 16; b /= 2)
     if (b <= cap && nx % b == 0) return b;
   return 16;
+}
+
+// s += x with the exact rounding error of the addition (Knuth's TwoSum, with
+// round-to-nearest intrinsics so that no step is contracted or re-associated)
+// added to the compensation c; s + c is the compensated sum.
+__device__ __forceinline__ void two_sum_acc(double& s, double& c, double x) {
+  const double t = __dadd_rn(s, x);
+  const double xp = __dsub_rn(t, s);
+  const double e = __dadd_rn(__dsub_rn(s, __dsub_rn(t, xp)), __dsub_rn(x, xp));
+  s = t;
+  c = __dadd_rn(c, e);
 }
 
 // Ordered bit pattern of a non-negative double for atomicMax.

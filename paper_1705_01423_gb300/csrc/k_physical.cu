@@ -430,6 +430,104 @@ cudaError_t cn_sweeps_adjoint(afid_ctx* c, double* gu, double* gv, double* gw, d
 // r = (b - mean_W b) - L phi, the convergence test on the correction norms,
 // and the final FP64 gauge (zero weighted mean of phi: the residual cannot
 // see a constant, so the FP32 corrections' gauge round-off is removed here).
+// ---------------------------------------------------------------------------
+// Wall-normal statistics (Sec. 3.2: statistics accumulated only along the
+// wall-normal direction, a vector reduction; Sec. 4: Nusselt number, wall
+// shear stress and friction Reynolds number). One block per face plane
+// k = 0..nz forms the horizontal means
+//   0 <u>  1 <v>  2 <u^2>  3 <v^2>            (cell plane k < nz)
+//   4 <w>  5 <w^2>  6 <T>  7 <T^2>  8 <w T>   (face plane k)
+// with per-thread partial sums in a fixed order (compensated for the first
+// moments) and the block sum added by warp 0 (deterministic).
+// prof: [nz+1][AFID_STAT_NQ].
+__global__ void __launch_bounds__(256) k_plane_stats(Grid g, const double* __restrict__ u,
+                                                     const double* __restrict__ v,
+                                                     const double* __restrict__ w,
+                                                     const double* __restrict__ T,
+                                                     double* __restrict__ prof) {
+  constexpr int NQ = AFID_STAT_NQ;
+  __shared__ double red[NQ][256];
+  const int k = blockIdx.x;
+  const size_t NXY = (size_t)g.nx * g.ny;
+  const size_t c0 = (size_t)k * NXY;
+  double s[NQ];
+  double e0 = 0.0, e1 = 0.0, e4 = 0.0, e6 = 0.0;  // compensations of the first moments
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) s[q] = 0.0;
+  const bool cell = k < g.nz;
+  for (size_t c = threadIdx.x; c < NXY; c += blockDim.x) {
+    if (cell) {
+      const double a = u[c0 + c], b = v[c0 + c];
+      two_sum_acc(s[0], e0, a);
+      two_sum_acc(s[1], e1, b);
+      s[2] = fma(a, a, s[2]);
+      s[3] = fma(b, b, s[3]);
+    }
+    const double ww = w[c0 + c];
+    two_sum_acc(s[4], e4, ww);
+    s[5] = fma(ww, ww, s[5]);
+    if (T) {
+      const double t = T[c0 + c];
+      two_sum_acc(s[6], e6, t);
+      s[7] = fma(t, t, s[7]);
+      s[8] = fma(ww, t, s[8]);
+    }
+  }
+  // the means enter differences across a wall cell (wall Nusselt numbers,
+  // wall shear stress), so their sums are compensated
+  s[0] += e0;
+  s[1] += e1;
+  s[4] += e4;
+  s[6] += e6;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] = s[q];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int q = 0; q < NQ; ++q) {
+      double t = 0.0;
+      for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) t += red[q][i];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) prof[(size_t)k * NQ + q] = t / (double)NXY;
+    }
+  }
+}
+
+// Scalars from the profiles (one thread; formulas of afid_stats in afid.h):
+// out[0..6] = nu_volume, nu_bottom, nu_top, tau_bottom, tau_top, re_tau, ke.
+__global__ void k_stats_scalars(Grid g, Metric m, afid_phys ph, const double* __restrict__ prof,
+                                double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  constexpr int NQ = AFID_STAT_NQ;
+  const int nz = g.nz;
+  double height = 0.0, wT = 0.0, kuv = 0.0, kw = 0.0;
+  for (int k = 0; k < nz; ++k) {
+    height += m.dzc[k];
+    kuv += m.dzc[k] * (prof[k * NQ + 2] + prof[k * NQ + 3]);
+  }
+  for (int k = 1; k < nz; ++k) {
+    wT += m.dzf[k] * prof[k * NQ + 8];
+    kw += m.dzf[k] * prof[k * NQ + 5];
+  }
+  const double dT = ph.T_bot - ph.T_top;
+  out[0] = ph.kappa > 0.0 ? 1.0 + (wT / height) / ph.kappa : 0.0;
+  out[1] = dT != 0.0 ? -(prof[1 * NQ + 6] - prof[0 * NQ + 6]) / m.dzc[0] / dT : 0.0;
+  out[2] = dT != 0.0 ? -(prof[nz * NQ + 6] - prof[(nz - 1) * NQ + 6]) / m.dzc[nz - 1] / dT : 0.0;
+  out[3] = ph.nu * (prof[0] - ph.u_bot) / (0.5 * m.dzc[0]);
+  out[4] = ph.nu * (ph.u_top - prof[(nz - 1) * NQ]) / (0.5 * m.dzc[nz - 1]);
+  const double u_tau = sqrt(0.5 * (fabs(out[3]) + fabs(out[4])));
+  out[5] = ph.nu > 0.0 ? 0.5 * height * u_tau / ph.nu : 0.0;
+  out[6] = 0.5 * (kuv + kw) / height;
+}
+
+cudaError_t statistics(afid_ctx* c, const double* u, const double* v, const double* w, const double* T) {
+  const Grid& g = c->g;
+  k_plane_stats<<<g.nz + 1, 256, 0, c->stream>>>(g, u, v, w, T, c->stat_buf);
+  k_stats_scalars<<<1, 32, 0, c->stream>>>(g, c->m, c->phys, c->stat_buf,
+                                           c->stat_buf + (size_t)(g.nz + 1) * AFID_STAT_NQ);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
 // Reduction of the per-block partials of the first mixed-precision forward
 // transform (k_r2c_x32<R32_FIRST>): weighted mean of b and ||b - mean||^2;
 // resets the refinement's scalars.

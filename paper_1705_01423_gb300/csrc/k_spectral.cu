@@ -91,13 +91,6 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   s = t;
   c = __fadd_rn(c, e);
 }
-__device__ __forceinline__ void two_sum_acc(double& s, double& c, double x) {
-  const double t = __dadd_rn(s, x);
-  const double xp = __dsub_rn(t, s);
-  const double e = __dadd_rn(__dsub_rn(s, __dsub_rn(t, xp)), __dsub_rn(x, xp));
-  s = t;
-  c = __dadd_rn(c, e);
-}
 
 // The part of x below its FP32 truncation to_real<float>(x), as an FP32
 // number (integer operations and one integer-to-float conversion: the 29
