@@ -6,8 +6,7 @@ substeps) against the FP64 oracle.
   4pi x 2pi x 1) on 64 x 32 x 32 cells for 50 steps; within 1e-12 relative L2
   after steps 1, 10 and the last.
 * The full sizes (512 x 512 x 384 and 1024 x 512 x 256) over 10 steps: the
-  growth of the difference is printed step by step (with each field's norm)
-  and bounded by 1e-10 at every step, i.e. the error growth is reported rather
+  growth of the difference is printed step by step and bounded by 1e-10 at every step, i.e. the error growth is reported rather
   than held to 1e-12. Fields that start at zero are round-off-dominated after
   the first step: in Rayleigh-Benard from rest u and v are the projection of a
   buoyancy-driven w of order 1e-6 (relative differences 1.9e-12 and 2.9e-12,
