@@ -76,8 +76,11 @@ struct Prof {
   long long n[KF_COUNT] = {};
 };
 
-// Arrays per variable set in the Crank-Nicolson table (k_cn_tables).
-constexpr int CN_TAB_ARRAYS = 7;
+// Arrays per variable set in the Crank-Nicolson table (k_cn_tables): sub,
+// m, c', sup, and the explicit-side coefficients 2 beta a, 2 beta c,
+// -2 beta (a + c); set 0 also carries the per-plane factors of the explicit
+// terms: alpha_l dt / dzf, dzc^-1 / 4, dzf^-1 / 4 (arrays 7, 8, 9).
+constexpr int CN_TAB_ARRAYS = 10;
 
 struct Grid {
   int nx, ny, nz;

@@ -279,6 +279,15 @@ __global__ void __launch_bounds__(96) k_cn_tables(Grid g, Metric m, int l, doubl
   const int k0 = o == 0 ? 0 : 1, k1 = g.nz;  // rows k0..nz-1
   const double* __restrict__ pa = o == 0 ? m.ca : m.fa;
   const double* __restrict__ pc = o == 0 ? m.cc : m.fc;
+  if (o == 0) {  // per-plane factors of the explicit terms (k_rhs_zm)
+    double* pz = ed + L;
+    const double adt = rk_alpha(l) * dt;
+    for (int k = lane; k < L; k += 32) {
+      pz[k] = adt * m.rdzf[k];
+      pz[L + k] = k < g.nz ? 0.25 * m.rdzc[k] : 0.0;
+      pz[2 * L + k] = 0.25 * m.rdzf[k];
+    }
+  }
   // every row's coefficients; diag_k -> mm[k] and sub_k sup_{k-1} -> cp[k]
   // as the chain's inputs (both overwritten by it)
   for (int k = k0 + lane; k < k1; k += 32) {

@@ -219,11 +219,10 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, P
     }
 
     // ---------------------------------------------------------------- u, v at cell k
-    const double rdzc = m.rdzc[k];
-    const double qz = 0.25 * rdzc;
+    const double qz = cnt[8 * L + k];  // dzc^-1 / 4
     {
-      const double A = (fxu - fxum) * qx + (Cjp - C) * qy + (fzu1 - fzu) * qz;
-      const double lap = fma(ujp + ujm, g.rdy2, (uip + uim) * g.rdx2) - lap0 * u0;
+      const double A = fma(fzu1 - fzu, qz, fma(Cjp - C, qy, (fxu - fxum) * qx));
+      const double lap = fma(-lap0, u0, fma(ujp + ujm, g.rdy2, (uip + uim) * g.rdx2));
       const double H = fma(ph.nu, lap, -A);
       const double z = fma(cnt[4 * L + k], ukm, fma(cnt[5 * L + k], ukp, fma(cnt[6 * L + k], u0, -cpx * (p0 - p[c + cim]))));
       double r = fma(cg, H, z);
@@ -232,8 +231,8 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, P
       Ru[c + col] = r;
     }
     {
-      const double A = (Cip - C) * qx + (fyv - fyvm) * qy + (fzv1 - fzv) * qz;
-      const double lap = fma(vjp + vjm, g.rdy2, (vip + vim) * g.rdx2) - lap0 * v0;
+      const double A = fma(fzv1 - fzv, qz, fma(fyv - fyvm, qy, (Cip - C) * qx));
+      const double lap = fma(-lap0, v0, fma(vjp + vjm, g.rdy2, (vip + vim) * g.rdx2));
       const double H = fma(ph.nu, lap, -A);
       const double z = fma(cnt[4 * L + k], vkm, fma(cnt[5 * L + k], vkp, fma(cnt[6 * L + k], v0, -cpy * (p0 - p[c + cjm]))));
       double r = fma(cg, H, z);
@@ -250,22 +249,21 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, P
         HT[(size_t)nz * NXY + col] = 0.0;
       }
     } else {
-      const double rdzf = m.rdzf[k];
-      const double qzf = 0.25 * rdzf;
+      const double qzf = cnt[9 * L + k];  // dzf^-1 / 4
       {
-        const double A = (fxw1 - fxw) * hx + (fyw1 - fyw) * hy + (fzw1 - fzw) * qzf;
-        const double lap = fma(wjp + wjm0, g.rdy2, (wip + wim0) * g.rdx2) - lap0 * w0;
+        const double A = fma(fzw1 - fzw, qzf, fma(fyw1 - fyw, hy, (fxw1 - fxw) * hx));
+        const double lap = fma(-lap0, w0, fma(wjp + wjm0, g.rdy2, (wip + wim0) * g.rdx2));
         double H = fma(ph.nu, lap, -A);
         if (HAS_T) H = fma(ph.buoy, t0, H);
-        const double z = fma(cnt[(CN_TAB_ARRAYS + 4) * L + k], wkm, fma(cnt[(CN_TAB_ARRAYS + 5) * L + k], wk1, fma(cnt[(CN_TAB_ARRAYS + 6) * L + k], w0, -ca_ * rdzf * (p0 - pkm))));
+        const double z = fma(cnt[(CN_TAB_ARRAYS + 4) * L + k], wkm, fma(cnt[(CN_TAB_ARRAYS + 5) * L + k], wk1, fma(cnt[(CN_TAB_ARRAYS + 6) * L + k], w0, -cnt[7 * L + k] * (p0 - pkm))));
         double r = fma(cg, H, z);
         if (l > 0) r = fma(cr, Hw[c + col], r);
         Hw[c + col] = H;
         Rw[c + col] = r;
       }
       if (HAS_T) {
-        const double A = (fxt1 - fxt) * hx + (fyt1 - fyt) * hy + (fzt1 - fzt) * qzf;
-        const double lap = fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2) - lap0 * t0;
+        const double A = fma(fzt1 - fzt, qzf, fma(fyt1 - fyt, hy, (fxt1 - fxt) * hx));
+        const double lap = fma(-lap0, t0, fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2));
         const double H = fma(ph.kappa, lap, -A);
         const double z = fma(cnt[(2 * CN_TAB_ARRAYS + 4) * L + k], tkm, fma(cnt[(2 * CN_TAB_ARRAYS + 5) * L + k], tk1, cnt[(2 * CN_TAB_ARRAYS + 6) * L + k] * t0));
         double r = fma(cg, H, z);
