@@ -22,6 +22,9 @@ computes (AFiD, arXiv 1705.01423), written in PyTorch CPU float64 ops:
                numbers, wall shear stress, friction Reynolds number (Sec. 3.2,
                Sec. 4)
   sampled.py   the Poisson solve at a few wavenumber pairs (large grids)
+  multires.py  temperature on a refined grid with a refined time step:
+               fine grid, trilinear prolongation of the velocity, restriction
+               of the temperature, the coupled step (Sec. 6)
 
 Coordinates follow the workloads, not the paper: x and y are the periodic,
 uniform directions and z is the bounded, stretched wall-normal direction (the
@@ -34,6 +37,6 @@ steady states, conservation identities, Runge-Kutta order conditions and
 finite differences).
 """
 from .grid import Grid
-from . import operators, poisson, timestep, adjoint
+from . import operators, poisson, timestep, adjoint, multires
 
-__all__ = ["Grid", "operators", "poisson", "timestep", "adjoint"]
+__all__ = ["Grid", "operators", "poisson", "timestep", "adjoint", "multires"]

@@ -121,11 +121,17 @@ def _zero_walls(f):
 
 
 # one RK3 substep ----------------------------------------------------------------
-def substep(g: Grid, ph: Phys, l: int, dt: float, state, Hprev):
+def substep(g: Grid, ph: Phys, l: int, dt: float, state, Hprev, advance_scalar: bool = True):
     """state = (u, v, w, T, p) (T may be None); Hprev = (Hu, Hv, Hw, HT) of the
-    previous substep (ignored at l = 0). Returns (new_state, H)."""
+    previous substep (ignored at l = 0). Returns (new_state, H).
+
+    advance_scalar=False: T only supplies the buoyancy of the w equation and is
+    returned unchanged (HT is None), as when the temperature lives on its own
+    refined grid and is advanced separately (multires.py)."""
     u, v, w, T, p = state
     Hu, Hv, Hw, HT = explicit_terms(g, ph, u, v, w, T)
+    if not advance_scalar:
+        HT = None
     if Hprev is None:
         Hprev = (None, None, None, None)
     gpu, gpv, gpw = op.gradient(g, p)
@@ -136,8 +142,8 @@ def substep(g: Grid, ph: Phys, l: int, dt: float, state, Hprev):
     us = u + cn_solve_cell(g, bn, Ru)
     vs = v + cn_solve_cell(g, bn, Rv)
     ws = w + cn_solve_face(g, bn, Rw)
-    Tn = None
-    if T is not None:
+    Tn = T if not advance_scalar else None
+    if T is not None and advance_scalar:
         RT = rk3_rhs(l, dt, HT, Hprev[3], ph.kappa * op.dzz_face(g, T))
         Tn = T + cn_solve_face(g, cn_beta(l, dt, ph.kappa), RT)
     s = ALPHA[l] * dt
