@@ -502,6 +502,85 @@ def side_measurements(ctx, w, dev, tma=True):
     out["poisson_fp64"]["families_ms"] = {k: v[0] for k, v in ctx.profile_read().items() if v[1]}
     ctx.profile(False)
     out["cufft_comparison"] = cufft_comparison(b, out, stream)
+    del b, phi64
+    try:
+        out["multires"] = multires_measurement(ctx, w, dev)
+    except Exception as e:  # report, do not hide
+        out["multires"] = {"error": str(e)}
+    return out
+
+
+def multires_measurement(ctx, w, dev, r=(2, 2, 2), n_sub=1, reps=3):
+    """Coupled step with the temperature on a grid refined r times (afid_mr_step):
+    the momentum step on the workload's grid with the restricted buoyancy, then
+    n_sub refined RK3/CN temperature steps on the fine grid."""
+    import torch
+    import synth
+    from paper_1705_01423_gb300 import MultiRes
+    stream = torch.cuda.current_stream()
+    m = MultiRes(ctx, *r)
+    zf = m.faces()
+    Tf = torch.as_tensor(synth.conduction_temperature(zf, m.ny, m.nx, w.T_bot, w.T_top, 11, amp=1e-3)).to(dev)
+    vel = [torch.as_tensor(a).to(dev) for a in synth.velocity_noise(w, 12, sigma=0.05)]
+    p = torch.zeros(ctx.cell, dtype=torch.float64, device=dev)
+    H = [torch.zeros(ctx.cell, dtype=torch.float64, device=dev), torch.zeros(ctx.cell, dtype=torch.float64, device=dev),
+         torch.zeros(ctx.face, dtype=torch.float64, device=dev)]
+    dt = 1e-3
+    ctx.project(*vel, p)  # a solenoidal start
+
+    def step():
+        m.step(dt, n_sub, *vel, p, *H, Tf)
+
+    ms = timed(step, reps, stream)
+    ctx.profile(True)
+    ctx.profile_read()
+    step()
+    fams = {k: v[0] for k, v in ctx.profile_read().items() if v[1]}
+    ctx.profile(False)
+    l0 = ctx.kernel_launches()
+    step()
+    torch.cuda.synchronize()
+    launches = ctx.kernel_launches() - l0
+    fine = m.nx * m.ny * m.nz
+    nsubst = 3 * n_sub  # refined substeps per coupled step
+    # FP64 operation model per fine point and substep: the temperature terms
+    # (36: face velocities 8, x/y fluxes 8, z flux 3, divergence 6, horizontal
+    # Laplacian 5, H 1, CN explicit side 3, R 2) and the prolongation (per
+    # component a z interpolation, 2, plus the bilinear value of a coarse
+    # plane, 6, shared by rz fine levels)
+    ops_rhs = 36.0 * fine * nsubst
+    ops_pro = 3 * (2.0 + 6.0 / r[2]) * fine * nsubst
+    peak = FP64_OPS_PEAK * 1e12
+    out = {"refinement": list(r), "n_sub": n_sub, "fine_grid": [m.nx, m.ny, m.nz],
+           "ms_per_coupled_step": ms, "fine_grid_points_per_s": fine / (ms / 1e3),
+           "kernel_launches_per_step": launches, "families_ms": fams,
+           "fp64_ops_frac": {"mr_scalar_rhs": ops_rhs / (fams.get("mr_scalar_rhs", 1e9) / 1e3) / peak,
+                             "mr_prolong": ops_pro / (fams.get("mr_prolong", 1e9) / 1e3) / peak},
+           "refined_workspace_gb": m.workspace_bytes / 1e9,
+           "note": "momentum %dx%dx%d (FP64 RK3/CN step, buoyancy from the restricted T), temperature "
+                   "%dx%dx%d (%d refined RK3/CN step(s) per momentum step)" % (w.nx, w.ny, w.nz, m.nx, m.ny, m.nz, n_sub)}
+    m.close()
+    del Tf, vel, p, H
+    # the single-grid step at the fine resolution, for the saving of the refined grid
+    try:
+        from paper_1705_01423_gb300 import Context, Physics
+        ph = Physics(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, u_bot=w.u_bot, u_top=w.u_top,
+                     T_bot=w.T_bot, T_top=w.T_top)
+        fctx = Context(out["fine_grid"][0], out["fine_grid"][1], out["fine_grid"][2], w.lx, w.ly, zf, phys=ph)
+        shp_c, shp_f = fctx.cell, fctx.face
+        S = [torch.zeros(shp_c, dtype=torch.float64, device=dev), torch.zeros(shp_c, dtype=torch.float64, device=dev),
+             torch.zeros(shp_f, dtype=torch.float64, device=dev),
+             torch.as_tensor(synth.conduction_temperature(zf, shp_c[1], shp_c[2], w.T_bot, w.T_top, 13, amp=1e-3)).to(dev),
+             torch.zeros(shp_c, dtype=torch.float64, device=dev)]
+        HS = [torch.zeros_like(S[0]), torch.zeros_like(S[1]), torch.zeros_like(S[2]), torch.zeros_like(S[3])]
+        ms_f = timed(lambda: fctx.rk3_step(S, HS, dt), 2, stream)
+        out["single_grid_step_at_fine_resolution_ms"] = ms_f
+        out["saving_vs_single_grid"] = ms_f / ms
+        fctx.close()
+        del S, HS
+    except Exception as e:  # report, do not hide
+        out["single_grid_step_at_fine_resolution_ms"] = {"error": str(e)}
+    torch.cuda.empty_cache()
     return out
 
 

@@ -150,8 +150,10 @@ afid_status afid_cfl(afid_ctx* ctx, const double* u, const double* v, const doub
  * correction with s = alpha_l dt. gamma = (8/15, 5/12, 3/4), rho = (0, -17/60,
  * -5/12), alpha = gamma + rho. H* arrays are in/out: on entry the previous
  * substep's explicit terms (unused when l = 0), on exit this substep's. T and
- * HT may both be NULL (no scalar). dt <= 0 uses the device-resident dt set by
- * afid_cfl. */
+ * HT may both be NULL (no scalar); T non-NULL with HT NULL makes T supply only
+ * the buoyancy of the w equation, unchanged by the call (the temperature is
+ * then advanced elsewhere, e.g. on the refined grid of afid_mr_*). dt <= 0
+ * uses the device-resident dt set by afid_cfl. */
 afid_status afid_rk3_substep(afid_ctx* ctx, int l, double dt, double* u, double* v, double* w,
                              double* T, double* p, double* Hu, double* Hv, double* Hw,
                              double* HT, afid_info* info);
@@ -210,6 +212,68 @@ afid_status afid_rk3_substep_adjoint(afid_ctx* ctx, int l, double dt, const doub
                                      double* gu, double* gv, double* gw, double* gT, double* gp,
                                      double* gHu, double* gHv, double* gHw, double* gHT);
 
+/* ---- Multiple-resolution temperature grid (Sec. 6, conclusions and future
+ * plans: the temperature on a grid finer than the momentum's, advanced with
+ * its own refined time step; the paper leaves the details to a cited paper,
+ * so the definitions below are this library's).
+ *
+ * Fine grid: every cell of the context's grid split into rx x ry x rz equal
+ * cells; fine face zf_f[rz k + m] = zf[k] + (zf[k+1] - zf[k]) m / rz, so coarse
+ * face k is fine face rz k. Fine fields are C-ordered like the coarse ones
+ * with (nxf, nyf, nzf) = (rx nx, ry ny, rz nz): velocity uf, vf [nzf][nyf][nxf],
+ * wf and the temperature Tf [nzf+1][nyf][nxf] (Tf planes 0 and nzf hold the
+ * wall temperatures and are not changed).
+ * Prolongation P: each velocity component is linear along each direction
+ * between its coarse staggered samples, evaluated at its fine staggered
+ * positions (periodic in x, y; along z, u and v reach their wall values u_bot /
+ * u_top and 0 on the walls, w is linear between coarse faces).
+ * Restriction R: coarse Tc[k][j][i] = mean of the rx x ry fine values of face
+ * plane rz k over coarse cell (i, j).
+ * Refined temperature step: the RK3/CN substep of afid_rk3_substep restricted
+ * to the temperature equation, on the fine grid with the fine velocity.
+ * All calls enqueue on the coarse context's stream; fine workspace (velocity,
+ * explicit terms, right-hand side, two coarse velocity copies, Tc) is
+ * allocated once by afid_mr_create. */
+typedef struct afid_mr afid_mr;
+
+/* 1 <= rx, ry, rz <= 8; the context must have the RK3 workspace (no
+ * AFID_POISSON_ONLY). AFID_ERR_OOM if the fine workspace does not fit. */
+afid_status afid_mr_create(afid_ctx* ctx, int rx, int ry, int rz, afid_mr** out);
+afid_status afid_mr_destroy(afid_mr* mr);
+afid_status afid_mr_dims(const afid_mr* mr, int* nxf, int* nyf, int* nzf);
+size_t afid_mr_workspace_bytes(const afid_mr* mr);
+/* The nzf+1 fine face coordinates into the HOST array zf_out. */
+afid_status afid_mr_faces(const afid_mr* mr, double* zf_out);
+
+/* Fine velocity at time t + theta dt: P((1 - theta) q0 + theta q1) for q = u,
+ * v, w (coarse device fields; u1, v1, w1 may be NULL when theta = 0), 0 <=
+ * theta <= 1, into the fine device fields uf, vf, wf. */
+afid_status afid_mr_prolong(afid_mr* mr, const double* u0, const double* v0, const double* w0,
+                            const double* u1, const double* v1, const double* w1, double theta,
+                            double* uf, double* vf, double* wf);
+
+/* Tc = R(Tf): Tf fine [nzf+1][nyf][nxf], Tc coarse [nz+1][ny][nx] (device). */
+afid_status afid_mr_restrict(afid_mr* mr, const double* Tf, double* Tc);
+
+/* Advances Tf from t to t + dt by n_sub >= 1 refined RK3/CN steps of dt / n_sub.
+ * Substep l of refined step s uses the velocity at its start time, t + theta dt
+ * with theta = (s + c_l) / n_sub, c = (0, 8/15, 2/3) (the partial sums of
+ * alpha), linear in time between the coarse states (u0, v0, w0) at t and (u1,
+ * v1, w1) at t + dt, prolonged. dt > 0 (host value). */
+afid_status afid_mr_scalar_advance(afid_mr* mr, double dt, int n_sub, const double* u0,
+                                   const double* v0, const double* w0, const double* u1,
+                                   const double* v1, const double* w1, double* Tf);
+
+/* One coupled step t -> t + dt: Tc = R(Tf); the three momentum substeps of
+ * afid_rk3_substep (l = 0, 1, 2) with buoyancy from Tc, held for the step
+ * (T non-NULL, HT NULL); then afid_mr_scalar_advance from the velocity at t to
+ * the velocity at t + dt. u, v, w, p, Hu, Hv, Hw: coarse device fields as in
+ * afid_rk3_substep (H* are scratch: substep 0 does not read them); Tf fine.
+ * info, when non-NULL, is filled by the last momentum substep. */
+afid_status afid_mr_step(afid_mr* mr, double dt, int n_sub, double* u, double* v, double* w,
+                         double* p, double* Hu, double* Hv, double* Hw, double* Tf,
+                         afid_info* info);
+
 /* Last status text. */
 const char* afid_status_string(afid_status s);
 
@@ -219,9 +283,11 @@ long long afid_kernel_launches(const afid_ctx* ctx);
 /* Instrumentation: when on, every launch group of the context is bracketed by
  * CUDA events on its stream, accumulated per kernel family (r2c_x, fft_y,
  * thomas, zero_mode, c2r_x, project, rhs, crank_nicolson, cfl_reduce, refine,
- * adjoint, cn_tables; AFID_KERNEL_FAMILIES of them). The first enable creates
+ * adjoint, cn_tables, mr_prolong, mr_scalar_rhs, mr_restrict; AFID_KERNEL_FAMILIES
+ * of them; the afid_mr_* calls of a refined grid record into its coarse
+ * context, their sweeps and tables under crank_nicolson and cn_tables). The first enable creates
  * the event pool (host-side CUDA events, no device memory). */
-#define AFID_KERNEL_FAMILIES 12
+#define AFID_KERNEL_FAMILIES 15
 afid_status afid_profile_enable(afid_ctx* ctx, int on);
 /* Synchronises the stream and returns, per family, the milliseconds and the
  * number of launch groups recorded since the last read (arrays of n entries,

@@ -88,9 +88,11 @@ def bracket_matrix(xc, xf) -> np.ndarray:
 
 
 def _apply(Mz, My, Mx, q):
-    """out[K][J][I] = sum Mz[K,k] My[J,j] Mx[I,i] q[k][j][i]."""
+    """out[K][J][I] = sum Mz[K,k] My[J,j] Mx[I,i] q[k][j][i], one axis at a time."""
     Mz, My, Mx = (torch.as_tensor(m, dtype=torch.float64) for m in (Mz, My, Mx))
-    return torch.einsum("Kk,Jj,Ii,kji->KJI", Mz, My, Mx, q)
+    q = torch.einsum("Ii,kji->kjI", Mx, q)
+    q = torch.einsum("Jj,kjI->kJI", My, q)
+    return torch.einsum("Kk,kJI->KJI", Mz, q)
 
 
 def prolong(g: Grid, gf: Grid, r, u, v, w, u_bot: float, u_top: float):

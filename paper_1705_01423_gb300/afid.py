@@ -87,8 +87,17 @@ _SIGS = {
     "afid_profile_read": (I, [P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), I]),
     "afid_kernel_family_name": (C.c_char_p, [I]),
     "afid_poisson_solve_noalloc": (I, [I, I, I, D, D, P, P, P, P]),
+    "afid_mr_create": (I, [P, I, I, I, C.POINTER(P)]),
+    "afid_mr_destroy": (I, [P]),
+    "afid_mr_dims": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
+    "afid_mr_workspace_bytes": (C.c_size_t, [P]),
+    "afid_mr_faces": (I, [P, P]),
+    "afid_mr_prolong": (I, [P, P, P, P, P, P, P, D, P, P, P]),
+    "afid_mr_restrict": (I, [P, P, P]),
+    "afid_mr_scalar_advance": (I, [P, D, I, P, P, P, P, P, P, P]),
+    "afid_mr_step": (I, [P, D, I, P, P, P, P, P, P, P, P, C.POINTER(Info)]),
 }
-KERNEL_FAMILIES = 12
+KERNEL_FAMILIES = 15
 
 
 def lib():
@@ -330,3 +339,95 @@ class Context:
             _ptr(gv, self.cell, "gv"), _ptr(gw, self.face, "gw"), _ptr(gT, self.face, "gT"),
             _ptr(gp, self.cell, "gp"), _ptr(gHu, self.cell, "gHu"), _ptr(gHv, self.cell, "gHv"),
             _ptr(gHw, self.face, "gHw"), _ptr(gHT, self.face, "gHT")), "afid_rk3_substep_adjoint")
+
+
+class MultiRes:
+    """Refined temperature grid over a Context (afid_mr_*): the grid refined
+    rx x ry x rz times, the velocity prolongation, the restriction of the
+    temperature and the refined temperature steps. Fine fields: velocity
+    cells `fcell` = (nzf, nyf, nxf), faces and temperature `fface` =
+    (nzf + 1, nyf, nxf)."""
+
+    def __init__(self, ctx: Context, rx: int, ry: int, rz: int):
+        self.ctx = ctx
+        self.r = (int(rx), int(ry), int(rz))
+        h = C.c_void_p()
+        _check(lib().afid_mr_create(ctx._h, self.r[0], self.r[1], self.r[2], C.byref(h)), "afid_mr_create")
+        self._h = h
+        a, b, c = I(), I(), I()
+        _check(lib().afid_mr_dims(h, C.byref(a), C.byref(b), C.byref(c)), "afid_mr_dims")
+        self.nx, self.ny, self.nz = a.value, b.value, c.value
+        self.workspace_bytes = int(lib().afid_mr_workspace_bytes(h))
+
+    def faces(self):
+        """The nzf + 1 fine face coordinates (numpy)."""
+        zf = np.zeros(self.nz + 1, dtype=np.float64)
+        _check(lib().afid_mr_faces(self._h, zf.ctypes.data_as(C.c_void_p)), "afid_mr_faces")
+        return zf
+
+    @property
+    def fcell(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def fface(self):
+        return (self.nz + 1, self.ny, self.nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().afid_mr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def prolong(self, vel0, vel1=None, theta=0.0, out=None):
+        """Fine (uf, vf, wf) at t + theta dt from the coarse states vel0 at t
+        and vel1 at t + dt."""
+        import torch
+        cc, cf = self.ctx.cell, self.ctx.face
+        u0, v0, w0 = vel0
+        if out is None:
+            out = (torch.empty(self.fcell, dtype=torch.float64, device=u0.device),
+                   torch.empty(self.fcell, dtype=torch.float64, device=u0.device),
+                   torch.empty(self.fface, dtype=torch.float64, device=u0.device))
+        u1, v1, w1 = vel1 if vel1 is not None else (None, None, None)
+        _check(lib().afid_mr_prolong(
+            self._h, _ptr(u0, cc, "u0"), _ptr(v0, cc, "v0"), _ptr(w0, cf, "w0"), _ptr(u1, cc, "u1"),
+            _ptr(v1, cc, "v1"), _ptr(w1, cf, "w1"), float(theta), _ptr(out[0], self.fcell, "uf"),
+            _ptr(out[1], self.fcell, "vf"), _ptr(out[2], self.fface, "wf")), "afid_mr_prolong")
+        return out
+
+    def restrict(self, Tf, Tc=None):
+        import torch
+        if Tc is None:
+            Tc = torch.empty(self.ctx.face, dtype=torch.float64, device=Tf.device)
+        _check(lib().afid_mr_restrict(self._h, _ptr(Tf, self.fface, "Tf"), _ptr(Tc, self.ctx.face, "Tc")),
+               "afid_mr_restrict")
+        return Tc
+
+    def scalar_advance(self, dt, n_sub, vel0, vel1, Tf):
+        cc, cf = self.ctx.cell, self.ctx.face
+        (u0, v0, w0), (u1, v1, w1) = vel0, vel1
+        _check(lib().afid_mr_scalar_advance(
+            self._h, float(dt), int(n_sub), _ptr(u0, cc, "u0"), _ptr(v0, cc, "v0"), _ptr(w0, cf, "w0"),
+            _ptr(u1, cc, "u1"), _ptr(v1, cc, "v1"), _ptr(w1, cf, "w1"), _ptr(Tf, self.fface, "Tf")),
+            "afid_mr_scalar_advance")
+
+    def step(self, dt, n_sub, u, v, w, p, Hu, Hv, Hw, Tf, info=False):
+        """One coupled step in place (momentum on the context's grid, Tf on
+        the fine grid)."""
+        cc, cf = self.ctx.cell, self.ctx.face
+        inf = Info() if info else None
+        st = lib().afid_mr_step(self._h, float(dt), int(n_sub), _ptr(u, cc, "u"), _ptr(v, cc, "v"),
+                                _ptr(w, cf, "w"), _ptr(p, cc, "p"), _ptr(Hu, cc, "Hu"), _ptr(Hv, cc, "Hv"),
+                                _ptr(Hw, cf, "Hw"), _ptr(Tf, self.fface, "Tf"), C.byref(inf) if inf else None)
+        _check(st, "afid_mr_step", allow=(AFID_ERR_NOT_CONVERGED, AFID_ERR_INCONSISTENT_RHS))
+        if info:
+            d = inf.as_dict()
+            d["status"] = st
+            return d
+        return None

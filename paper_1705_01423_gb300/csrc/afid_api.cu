@@ -10,6 +10,51 @@
 
 using namespace afid;
 
+namespace afid {
+
+void metric_host(int nz, double rdx2, double rdy2, const double* zf, std::vector<double>& flat,
+                 std::vector<size_t>& offs) {
+  std::vector<double> dzc(nz), rdzc(nz), dzf(nz + 1), rdzf(nz + 1), pa(nz, 0.0), pc(nz, 0.0),
+      ca(nz), cc(nz), fa(nz + 1, 0.0), fc(nz + 1, 0.0), wlo(nz + 1, 0.0), whi(nz + 1, 0.0),
+      pdiag(nz);
+  for (int k = 0; k < nz; ++k) {
+    dzc[k] = zf[k + 1] - zf[k];
+    rdzc[k] = 1.0 / dzc[k];
+  }
+  dzf[0] = 0.5 * dzc[0];
+  dzf[nz] = 0.5 * dzc[nz - 1];
+  for (int k = 1; k < nz; ++k) dzf[k] = 0.5 * (zf[k] + zf[k + 1]) - 0.5 * (zf[k - 1] + zf[k]);
+  for (int k = 0; k <= nz; ++k) rdzf[k] = 1.0 / dzf[k];
+  for (int k = 0; k < nz; ++k) {
+    if (k > 0) pa[k] = 1.0 / (dzc[k] * dzf[k]);
+    if (k < nz - 1) pc[k] = 1.0 / (dzc[k] * dzf[k + 1]);
+    ca[k] = 1.0 / (dzc[k] * dzf[k]);
+    cc[k] = 1.0 / (dzc[k] * dzf[k + 1]);
+  }
+  for (int k = 0; k < nz; ++k) pdiag[k] = pa[k] + pc[k] + 2.0 * rdx2 + 2.0 * rdy2;
+  for (int k = 1; k < nz; ++k) {
+    fa[k] = 1.0 / (dzf[k] * dzc[k - 1]);
+    fc[k] = 1.0 / (dzf[k] * dzc[k]);
+    wlo[k] = dzc[k - 1] / (2.0 * dzf[k]);
+    whi[k] = dzc[k] / (2.0 * dzf[k]);
+  }
+  const std::vector<double>* arrs[] = {&dzc, &rdzc, &dzf, &rdzf, &pa, &pc, &ca, &cc, &fa, &fc, &wlo, &whi, &pdiag};
+  flat.clear();
+  offs.clear();
+  for (auto* a : arrs) {
+    offs.push_back(flat.size());
+    flat.insert(flat.end(), a->begin(), a->end());
+  }
+}
+
+Metric metric_view(const double* mb, const std::vector<size_t>& offs) {
+  return Metric{mb + offs[0], mb + offs[1], mb + offs[2], mb + offs[3], mb + offs[4], mb + offs[5],
+                mb + offs[6], mb + offs[7], mb + offs[8], mb + offs[9], mb + offs[10], mb + offs[11],
+                mb + offs[12]};
+}
+
+}  // namespace afid
+
 namespace {
 
 // n = 2^a 3^b 5^c (the radices of the FFT passes)
@@ -101,6 +146,8 @@ void free_all(afid_ctx* c) {
                 c->part, c->part2, c->part3, c->rres, c->dprev, c->cff, c->stat_buf};
   for (void* p : ps)
     if (p) cudaFree(p);
+  delete[] c->zf_host;
+  c->zf_host = nullptr;
 }
 
 afid_status fill_info(afid_ctx* c, afid_info* info, bool mixed, bool want_div) {
@@ -231,39 +278,20 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   }
   const bool mixed = c->prec == AFID_MIXED;
 
+  c->zf_host = new (std::nothrow) double[nz + 1];
+  if (!c->zf_host) {
+    delete c;
+    return AFID_ERR_OOM;
+  }
+  std::memcpy(c->zf_host, desc->zf, (nz + 1) * sizeof(double));
+
   // ---- host metric (wall-normal)
-  std::vector<double> dzc(nz), rdzc(nz), dzf(nz + 1), rdzf(nz + 1), pa(nz, 0.0), pc(nz, 0.0),
-      ca(nz), cc(nz), fa(nz + 1, 0.0), fc(nz + 1, 0.0), wlo(nz + 1, 0.0), whi(nz + 1, 0.0),
-      pdiag(nz);
-  const double* zf = desc->zf;
-  for (int k = 0; k < nz; ++k) {
-    dzc[k] = zf[k + 1] - zf[k];
-    rdzc[k] = 1.0 / dzc[k];
-  }
-  dzf[0] = 0.5 * dzc[0];
-  dzf[nz] = 0.5 * dzc[nz - 1];
-  for (int k = 1; k < nz; ++k) dzf[k] = 0.5 * (zf[k] + zf[k + 1]) - 0.5 * (zf[k - 1] + zf[k]);
-  for (int k = 0; k <= nz; ++k) rdzf[k] = 1.0 / dzf[k];
-  for (int k = 0; k < nz; ++k) {
-    if (k > 0) pa[k] = 1.0 / (dzc[k] * dzf[k]);
-    if (k < nz - 1) pc[k] = 1.0 / (dzc[k] * dzf[k + 1]);
-    ca[k] = 1.0 / (dzc[k] * dzf[k]);
-    cc[k] = 1.0 / (dzc[k] * dzf[k + 1]);
-  }
-  for (int k = 0; k < nz; ++k) pdiag[k] = pa[k] + pc[k] + 2.0 * g.rdx2 + 2.0 * g.rdy2;
-  for (int k = 1; k < nz; ++k) {
-    fa[k] = 1.0 / (dzf[k] * dzc[k - 1]);
-    fc[k] = 1.0 / (dzf[k] * dzc[k]);
-    wlo[k] = dzc[k - 1] / (2.0 * dzf[k]);
-    whi[k] = dzc[k] / (2.0 * dzf[k]);
-  }
-  const std::vector<double>* arrs[] = {&dzc, &rdzc, &dzf, &rdzf, &pa, &pc, &ca, &cc, &fa, &fc, &wlo, &whi, &pdiag};
   std::vector<double> flat;
   std::vector<size_t> offs;
-  for (auto* a : arrs) {
-    offs.push_back(flat.size());
-    flat.insert(flat.end(), a->begin(), a->end());
-  }
+  metric_host(nz, g.rdx2, g.rdy2, desc->zf, flat, offs);
+  const double* pa = flat.data() + offs[4];
+  const double* pc = flat.data() + offs[5];
+  const double* pdiag = flat.data() + offs[12];
 
   // ---- host tables
   std::vector<double2> twx(nx), twy(ny);
@@ -350,10 +378,7 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     delete c;
     return AFID_ERR_OOM;
   }
-  const double* mb = static_cast<const double*>(c->metric_buf);
-  c->m = Metric{mb + offs[0], mb + offs[1], mb + offs[2], mb + offs[3], mb + offs[4], mb + offs[5],
-                mb + offs[6], mb + offs[7], mb + offs[8], mb + offs[9], mb + offs[10], mb + offs[11],
-                mb + offs[12]};
+  c->m = metric_view(static_cast<const double*>(c->metric_buf), offs);
   bool ok = true;
   auto up = [&](void* dst, const void* src, size_t bytes) {
     if (dst && bytes) ok = ok && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -465,7 +490,7 @@ afid_status afid_profile_read(afid_ctx* c, double* ms, long long* launches, int 
 const char* afid_kernel_family_name(int f) {
   static const char* names[] = {"r2c_x", "fft_y", "thomas", "zero_mode", "c2r_x", "project",
                                 "rhs", "crank_nicolson", "cfl_reduce", "refine", "adjoint",
-                                "cn_tables"};
+                                "cn_tables", "mr_prolong", "mr_scalar_rhs", "mr_restrict"};
   return (f >= 0 && f < KF_COUNT) ? names[f] : "unknown";
 }
 
@@ -522,11 +547,12 @@ afid_status afid_rk3_substep(afid_ctx* c, int l, double dt, double* u, double* v
   if (l < 0 || l > 2 || !std::isfinite(dt)) return AFID_ERR_INVALID_ARG;
   afid_status st = check_fields({u, v, w, p, Hu, Hv, Hw});
   if (st) return st;
-  if ((T == nullptr) != (HT == nullptr)) return AFID_ERR_INVALID_ARG;
-  if (T && (st = check_fields({T, HT}))) return st;
+  if (HT && !T) return AFID_ERR_INVALID_ARG;
+  if (T && (st = check_fields({T}))) return st;
+  if (HT && (st = check_fields({HT}))) return st;
   if (cn_tables(c, l, dt)) return AFID_ERR_CUDA;
   if (rk3_explicit(c, l, dt, u, v, w, T, p, Hu, Hv, Hw, HT)) return AFID_ERR_CUDA;
-  if (cn_sweeps(c, u, v, w, T)) return AFID_ERR_CUDA;
+  if (cn_sweeps(c, u, v, w, HT ? T : nullptr)) return AFID_ERR_CUDA;
   st = solve_any(c, nullptr, u, v, w, true, c->phi, info != nullptr);
   if (st) return st;
   if (project(c, u, v, w, p, c->phi)) return AFID_ERR_CUDA;

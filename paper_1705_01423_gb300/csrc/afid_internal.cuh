@@ -63,6 +63,9 @@ enum KFam {
   KF_REFINE,    // mixed-precision residual, norms, checks
   KF_ADJ,       // adjoint-only kernels
   KF_CNTAB,     // Crank-Nicolson factor tables (one tiny kernel per substep)
+  KF_MR_PROLONG,   // refined temperature grid: velocity prolongation (+ time interpolation)
+  KF_MR_RHS,       // refined temperature grid: explicit terms and right-hand side
+  KF_MR_RESTRICT,  // refined temperature grid: restriction to the momentum grid
   KF_COUNT
 };
 
@@ -146,6 +149,8 @@ struct afid_ctx {
   float2* cff;
   // wall-normal statistics: profiles [nz+1][AFID_STAT_NQ] and 8 scalars
   double* stat_buf;
+  // host copy of the nz+1 face coordinates (refined grids are built from it)
+  double* zf_host;
   size_t bytes;
   long long launches;
   afid::Prof* prof;
@@ -158,6 +163,13 @@ struct afid_ctx {
 };
 
 namespace afid {
+
+// Host wall-normal metric of the faces zf[0..nz] (the arrays of Metric, in its
+// order, concatenated in `flat`, offsets in `offs`), and the device view of
+// its uploaded copy.
+void metric_host(int nz, double rdx2, double rdy2, const double* zf, std::vector<double>& flat,
+                 std::vector<size_t>& offs);
+Metric metric_view(const double* dev, const std::vector<size_t>& offs);
 
 // launchers (stream-ordered; return cudaError_t of the launch)
 cudaError_t init_thomas_tables(afid_ctx* c);
@@ -199,6 +211,12 @@ cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const d
 cudaError_t cn_tables(afid_ctx* c, int l, double dt);
 cudaError_t cn_sweeps(afid_ctx* c, double* u, double* v, double* w, double* T);
 cudaError_t scale_cells(afid_ctx* c, const double* in, double* out, bool forward);
+// The Crank-Nicolson tables of substep l for any grid and metric (into tab,
+// with the substep scalars in scal), and the forward sweep of the temperature
+// operator alone: T += A^-1 RT on the interior faces (RT overwritten).
+cudaError_t cn_tables_grid(const Grid& g, const Metric& m, int l, double dt, double* scal, double nu,
+                           double kappa, double* tab, cudaStream_t st);
+cudaError_t cn_sweep_scalar(const Grid& g, const double* tab, double* RT, double* T, cudaStream_t st);
 cudaError_t adjoint_explicit(afid_ctx* c, int l, double dt, const double* u, const double* v,
                              const double* w, const double* T, double* gu, double* gv,
                              double* gw, double* gT, double* gp, double* gHu, double* gHv,

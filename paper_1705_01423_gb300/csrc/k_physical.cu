@@ -424,6 +424,20 @@ cudaError_t cn_sweeps(afid_ctx* c, double* u, double* v, double* w, double* T) {
   return cudaGetLastError();
 }
 
+cudaError_t cn_tables_grid(const Grid& g, const Metric& m, int l, double dt, double* scal, double nu,
+                           double kappa, double* tab, cudaStream_t st) {
+  k_cn_tables<<<1, 96, 0, st>>>(g, m, l, dt, scal, nu, kappa, tab);
+  return cudaGetLastError();
+}
+
+cudaError_t cn_sweep_scalar(const Grid& g, const double* tab, double* RT, double* T, cudaStream_t st) {
+  const size_t NXY = (size_t)g.nx * g.ny;
+  dim3 grd(ceil_div((long long)NXY, 128), 4);  // the blocks of variables 0-2 return at once
+  k_cn_sweep<false><<<grd, 128, 0, st>>>(g, tab, nullptr, nullptr, nullptr, RT, nullptr, nullptr,
+                                         nullptr, T);
+  return cudaGetLastError();
+}
+
 cudaError_t cn_sweeps_adjoint(afid_ctx* c, double* gu, double* gv, double* gw, double* gT) {
   ProfScope ps(c, KF_CN);
   const size_t NXY = (size_t)c->g.nx * c->g.ny;

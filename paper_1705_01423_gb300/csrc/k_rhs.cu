@@ -37,7 +37,9 @@ struct PhysR {
 // WPR warps per block row: 1 (BX = min(32, nx), BY = 8) or 2 (BX = 64, BY = 4;
 // the two warps of a row pass their facing edge fluxes through shared
 // memory, so only the block's outer edges recompute neighbour fluxes).
-template <bool HAS_T, int BY, int WPR>
+// TM: 0 no temperature, 1 temperature advanced (HT, RT written), 2 T only
+// supplies the buoyancy of the w equation (T kept on another grid).
+template <int TM, int BY, int WPR>
 __global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR ph, int l, double dt_in,
                                                     const double* __restrict__ scal,
                                                     const double* __restrict__ u,
@@ -50,6 +52,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, P
                                                     double* __restrict__ Ru, double* __restrict__ Rv,
                                                     double* __restrict__ Rw, double* __restrict__ RT,
                                                     const double* __restrict__ cnt, int kchunk) {
+  constexpr bool HAS_T = TM == 1, BUOY = TM != 0;
   const int BX = blockDim.x;  // min(32, nx) or 64
   const int SW = WPR == 1 ? BX : 32;  // shuffle width: one block row per warp segment
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, P
   const size_t c0 = (size_t)k0 * NXY;
   double u0 = u[c0 + col], v0 = v[c0 + col];
   double w0 = w[c0 + col], wk1 = w[c0 + NXY + col];
-  double t0 = HAS_T ? T[c0 + col] : 0.0, tk1 = HAS_T ? T[c0 + NXY + col] : 0.0;
+  double t0 = BUOY ? T[c0 + col] : 0.0, tk1 = BUOY ? T[c0 + NXY + col] : 0.0;
   double wim0 = w[c0 + cim], wjm0 = w[c0 + cjm];  // face k at (i-1), (j-1)
   double fzu = 0.0, fzv = 0.0;          // u, v z-fluxes through face k (wall: 0)
   double fzw = 0.0, fzt = 0.0;          // w, T z-fluxes at cell k-1
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, P
         const double A = fma(fzw1 - fzw, qzf, fma(fyw1 - fyw, hy, (fxw1 - fxw) * hx));
         const double lap = fma(-lap0, w0, fma(wjp + wjm0, g.rdy2, (wip + wim0) * g.rdx2));
         double H = fma(ph.nu, lap, -A);
-        if (HAS_T) H = fma(ph.buoy, t0, H);
+        if (BUOY) H = fma(ph.buoy, t0, H);
         const double z = fma(cnt[(CN_TAB_ARRAYS + 4) * L + k], wkm, fma(cnt[(CN_TAB_ARRAYS + 5) * L + k], wk1, fma(cnt[(CN_TAB_ARRAYS + 6) * L + k], w0, -cnt[7 * L + k] * (p0 - pkm))));
         double r = fma(cg, H, z);
         if (l > 0) r = fma(cr, Hw[c + col], r);
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, P
       wim0 = wk1im;
       wjm0 = wk1jm;
       wk1 = w[c + 2 * NXY + col];
-      if (HAS_T) tk1 = T[c + 2 * NXY + col];
+      if (BUOY) tk1 = T[c + 2 * NXY + col];
     }
   }
 }
@@ -321,12 +324,15 @@ cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const d
   k_rhs_zm<HT_, BY_, W_><<<grd, blk, 0, c->stream>>>(g, c->m, ph, l, dt, c->scal, u, v, w, T, p, Hu, Hv, \
                                                      Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3],         \
                                                      c->cntab, kchunk)
-  if (T) {
-    if (wide) AFID_RHS(true, 4, 2);
-    else AFID_RHS(true, 8, 1);
+  if (T && HT) {
+    if (wide) AFID_RHS(1, 4, 2);
+    else AFID_RHS(1, 8, 1);
+  } else if (T) {
+    if (wide) AFID_RHS(2, 4, 2);
+    else AFID_RHS(2, 8, 1);
   } else {
-    if (wide) AFID_RHS(false, 4, 2);
-    else AFID_RHS(false, 8, 1);
+    if (wide) AFID_RHS(0, 4, 2);
+    else AFID_RHS(0, 8, 1);
   }
 #undef AFID_RHS
   c->launches++;

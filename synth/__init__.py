@@ -137,6 +137,20 @@ def rb_initial(w: Workload, seed: int, amp: float = 1e-3):
     return u, v, ww, T, p
 
 
+def conduction_temperature(zf, ny: int, nx: int, T_bot: float, T_top: float, seed: int,
+                           amp: float = 1e-3) -> np.ndarray:
+    """Conduction profile T = T_bot + (T_top - T_bot) z on the given face
+    coordinates zf (nz+1 of them, any grid, e.g. a refined temperature grid)
+    plus U(-amp, amp) noise on the interior faces: [nz+1][ny][nx]."""
+    g = rng(seed)
+    zf = np.asarray(zf, dtype=np.float64)
+    T = np.empty((len(zf), ny, nx))
+    T[:] = (T_bot + (T_top - T_bot) * zf)[:, None, None]
+    if amp != 0.0:
+        T[1:-1] += g.uniform(-amp, amp, size=(len(zf) - 2, ny, nx))
+    return T
+
+
 def couette_initial(w: Workload, seed: int, sigma: float = 0.05):
     """Plane Couette start: laminar u = u_bot + (u_top-u_bot) zc plus N(0, sigma^2) on
     u, v, w (w zero on the walls); pressure zero."""
