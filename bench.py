@@ -58,6 +58,8 @@ def parse():
                     help="only the Poisson-solve side measurement (FP64 and mixed)")
     ap.add_argument("--no-tma", action="store_true",
                     help="use the plain y-transform kernel instead of the TMA-staged one")
+    ap.add_argument("--multires-only", action="store_true",
+                    help="only the refined-temperature-grid coupled step (2x2x2, afid_mr_step)")
     ap.add_argument("--grid", default=None,
                     help="override the workload's cells as NXxNYxNZ (profiling smaller cases)")
     return ap.parse_args()
@@ -279,6 +281,19 @@ def run_poisson_only(args):
                             "err_estimate": info["err_estimate"], "speedup_vs_fp64": ms64 / msm,
                             "families_ms": famm}
     print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "tma_y": tma, "poisson": out}))
+
+
+def run_multires_only(args):
+    """The refined-temperature-grid measurement alone on the workload grid."""
+    import torch
+    from paper_1705_01423_gb300 import Context, Physics
+    w = workload_from(args)
+    dev = torch.device("cuda", 0)
+    ph = Physics(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, u_bot=w.u_bot, u_top=w.u_top,
+                 T_bot=w.T_bot, T_top=w.T_top)
+    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), phys=ph)
+    out = multires_measurement(ctx, w, dev)
+    print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "multires": out}))
 
 
 def run_ours(args):
@@ -640,6 +655,8 @@ def main():
         run_reference(args)
     elif args.poisson_only:
         run_poisson_only(args)
+    elif args.multires_only:
+        run_multires_only(args)
     else:
         run_ours(args)
 

@@ -108,6 +108,74 @@ __global__ void __launch_bounds__(256) k_mr_prolong(Grid gc, Grid gf, MrTab t,
   }
 }
 
+// The same prolongation for blocks of 32 x 8 fine columns (nx_f a multiple
+// of 32, ny_f of 8): the x interpolation of the coarse rows the block needs
+// (at most MR_ROWS of them) is formed once per coarse plane in shared memory
+// and shared by the fine rows between them, then each thread interpolates in
+// y and z. Per fine column and coarse plane: one y interpolation plus its
+// share of the x interpolations (about 2/ry + 1/4 of one), against three.
+// Every branch on the plane index is uniform over the block (the tables
+// depend on K only), so the barriers inside it are reached by all threads.
+constexpr int MR_ROWS = 10;
+template <bool CELL>
+__global__ void __launch_bounds__(256) k_mr_prolong_sep(Grid gc, Grid gf, MrTab t,
+                                                        const double* __restrict__ q, double qbot,
+                                                        double qtop, double* __restrict__ out, int kchunk) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int X = blockIdx.x * 32 + tx, Y = blockIdx.y * 8 + ty;
+  const int nx = gc.nx, ny = gc.ny;
+  const size_t NXYc = (size_t)nx * ny, NXYf = (size_t)gf.nx * gf.ny;
+  __shared__ double xr[2][MR_ROWS][32];
+  // coarse rows of the block: jr0, jr0 + 1, ... (mod ny); this thread's two
+  const int jr0 = t.iy[blockIdx.y * 8];
+  int nrows = t.iy[blockIdx.y * 8 + 7] - jr0;
+  if (nrows < 0) nrows += ny;
+  nrows += 2;
+  int r0 = t.iy[Y] - jr0;
+  if (r0 < 0) r0 += ny;
+  const double wy = t.wy[Y];
+  // the x-interpolation task of this thread: (row, column) pairs tid, tid + 256
+  const int nx_tasks = nrows * 32;
+  // Bilinear value of coarse plane kc. The two buffers alternate between
+  // calls, so a buffer is rewritten only after the barrier of the call in
+  // between, which every thread reaches after reading it.
+  int b = 0;
+  auto plane = [&](int kc) {
+    const double* p = q + (size_t)kc * NXYc;
+    for (int a = tid; a < nx_tasks; a += 256) {
+      const int row = a >> 5, xc = a & 31;
+      int jr = jr0 + row;
+      if (jr >= ny) jr -= ny;
+      const int Xa = blockIdx.x * 32 + xc;
+      const int i0 = t.ix[Xa], i1 = wrap_next(i0, nx);
+      const double* pr = p + (size_t)jr * nx;
+      xr[b][row][xc] = fma(t.wx[Xa], pr[i1] - pr[i0], pr[i0]);
+    }
+    __syncthreads();
+    const double lo = xr[b][r0][tx], hi = xr[b][r0 + 1][tx];
+    b ^= 1;
+    return fma(wy, hi - lo, lo);
+  };
+  auto ext = [&](int e) -> double {
+    if (CELL) return e == 0 ? qbot : (e == gc.nz + 1 ? qtop : plane(e - 1));
+    return plane(e);
+  };
+  const int nK = CELL ? gf.nz : gf.nz + 1;
+  const int K0 = blockIdx.z * kchunk, K1 = min(nK, K0 + kchunk);
+  const size_t col = (size_t)Y * gf.nx + X;
+  int cur = -2;
+  double lo = 0.0, hi = 0.0;
+  for (int K = K0; K < K1; ++K) {
+    const int e = t.iz[K];
+    if (e != cur) {  // uniform: e depends on K only
+      lo = e == cur + 1 ? hi : ext(e);
+      hi = ext(e + 1);
+      cur = e;
+    }
+    out[(size_t)K * NXYf + col] = fma(t.wz[K], hi - lo, lo);
+  }
+}
+
 // out_f = a_f + theta (b_f - a_f) for the three coarse velocity fields
 // (blockIdx.y = component; u, v: n cells, w: n + NXY faces).
 __global__ void k_mr_lerp(size_t n, size_t nxy, double theta, const double* __restrict__ a0,
@@ -221,6 +289,95 @@ __global__ void __launch_bounds__(256) k_mr_scalar_rhs(Grid g, Metric m, double 
   }
 }
 
+// The same terms with the x and y face fluxes shared between neighbours
+// (blocks of BY rows of 32 WPR points; nx a multiple of 32 WPR, ny of BY).
+// Each thread forms the flux through its own left (x) and lower (y) face;
+// the right-face flux comes from the next lane (shuffle), across the two warps
+// of a 64-wide row through shared memory, and is formed directly only at the
+// block's right edge; the upper-face flux comes from the next row through a
+// double-buffered shared array (one barrier per k), formed directly only in
+// the block's last row. Masked lanes cost the same issue slots, so an edge
+// branch costs its warp the full instruction count: wider blocks have fewer.
+template <int BY, int WPR>
+__global__ void __launch_bounds__(32 * WPR * BY, 2) k_mr_scalar_rhs_sh(
+    Grid g, Metric m, double kappa, int l, double dt, const double* __restrict__ u,
+    const double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ T,
+    double* __restrict__ HT, double* __restrict__ RT, const double* __restrict__ cnt, int kchunk) {
+  constexpr int BX = 32 * WPR;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
+  const int nx = g.nx, nz = g.nz;
+  const size_t NXY = (size_t)nx * g.ny;
+  const int ip = wrap_next(i, nx), im = wrap_prev(i, nx);
+  const int jp = wrap_next(j, g.ny), jm = wrap_prev(j, g.ny);
+  const size_t col = (size_t)j * nx + i;
+  const size_t cip = (size_t)j * nx + ip, cim = (size_t)j * nx + im;
+  const size_t cjp = (size_t)jp * nx + i, cjm = (size_t)jm * nx + i;
+  const int L = nz + 1;
+  const double cg = dt * rk_gamma(l), cr = dt * rk_rho(l);
+  const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
+  const double lap0 = 2.0 * (g.rdx2 + g.rdy2);
+  const double* __restrict__ ea = cnt + (size_t)(2 * CN_TAB_ARRAYS + 4) * L;
+  const double* __restrict__ ec = ea + L;
+  const double* __restrict__ ed = ec + L;
+  const double* __restrict__ qzf = cnt + (size_t)9 * L;
+  const bool last_x = tx == BX - 1, last_row = ty == BY - 1;
+  __shared__ double sfy[2][BY][BX];  // lower-face y flux of every thread
+  __shared__ double sfx[2][BY];      // left-face x flux of x = 32 (second warp of a row)
+
+  const int kb = blockIdx.z * kchunk;
+  const int k0 = max(1, kb), k1 = min(nz, kb + kchunk);
+  if (blockIdx.z == 0) {
+    HT[col] = 0.0;
+    HT[(size_t)nz * NXY + col] = 0.0;
+  }
+  if (k0 >= k1) return;  // uniform over the block
+  size_t c = (size_t)(k0 - 1) * NXY;
+  double ukm = u[c + col], vkm = v[c + col];
+  double tkm = T[c + col], wkm = w[c + col];
+  double t0 = T[c + NXY + col], w0 = w[c + NXY + col];
+  double fz0 = (wkm + w0) * (tkm + t0);
+  for (int k = k0; k < k1; ++k) {
+    c = (size_t)k * NXY;
+    const int buf = k & 1;
+    const double uk = u[c + col], vk = v[c + col];
+    const double tk1 = T[c + NXY + col], wk1 = w[c + NXY + col];
+    const double tip = T[c + cip], tim = T[c + cim], tjp = T[c + cjp], tjm = T[c + cjm];
+    const double wlo = m.wlo[k], whi = m.whi[k];
+    const double fxl = fma(wlo, ukm, whi * uk) * (tim + t0);
+    const double fyb = fma(wlo, vkm, whi * vk) * (tjm + t0);
+    sfy[buf][ty][tx] = fyb;
+    if (WPR == 2 && tx == 32) sfx[buf][ty] = fxl;
+    __syncthreads();
+    double fxr = __shfl_down_sync(FULL, fxl, 1);
+    if (WPR == 2 && tx == 31) fxr = sfx[buf][ty];
+    if (__any_sync(FULL, last_x)) {
+      if (last_x) fxr = fma(wlo, u[c - NXY + cip], whi * u[c + cip]) * (t0 + tip);
+    }
+    double fyt;
+    if (last_row)  // the whole warp (one row) takes this branch
+      fyt = fma(wlo, v[c - NXY + cjp], whi * v[c + cjp]) * (t0 + tjp);
+    else
+      fyt = sfy[buf][ty + 1][tx];
+    const double fz1 = (w0 + wk1) * (t0 + tk1);
+    const double A = fma(fz1 - fz0, qzf[k], fma(fyt - fyb, hy, (fxr - fxl) * hx));
+    const double lap = fma(-lap0, t0, fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2));
+    const double H = fma(kappa, lap, -A);
+    const double z = fma(ea[k], tkm, fma(ec[k], tk1, ed[k] * t0));
+    double r = fma(cg, H, z);
+    if (l > 0) r = fma(cr, HT[c + col], r);
+    HT[c + col] = H;
+    RT[c + col] = r;
+    ukm = uk;
+    vkm = vk;
+    tkm = t0;
+    t0 = tk1;
+    w0 = wk1;
+    fz0 = fz1;
+  }
+}
+
 // z chunking so that a launch has about sixteen 256-thread blocks per SM
 int z_chunk(const afid_ctx* c, long long blocks_per_plane, int levels) {
   const long long want = 16LL * c->num_sms;
@@ -248,10 +405,19 @@ cudaError_t prolong(afid_mr* mr, const double* u, const double* v, const double*
   const int kc_c = z_chunk(c, bpp, gf.nz), kc_f = z_chunk(c, bpp, gf.nz + 1);
   dim3 gc_(ceil_div(gf.nx, 32), ceil_div(gf.ny, 8), ceil_div(gf.nz, kc_c));
   dim3 gf_(ceil_div(gf.nx, 32), ceil_div(gf.ny, 8), ceil_div(gf.nz + 1, kc_f));
-  k_mr_prolong<true><<<gc_, blk, 0, c->stream>>>(c->g, gf, tables_for(mr, 0), u, c->phys.u_bot,
-                                                 c->phys.u_top, uf, kc_c);
-  k_mr_prolong<true><<<gc_, blk, 0, c->stream>>>(c->g, gf, tables_for(mr, 1), v, 0.0, 0.0, vf, kc_c);
-  k_mr_prolong<false><<<gf_, blk, 0, c->stream>>>(c->g, gf, tables_for(mr, 2), w, 0.0, 0.0, wf, kc_f);
+  // shared x interpolation when the 32 x 8 blocks tile the fine plane (the
+  // rows a block needs: at most 8/ry + 2 <= MR_ROWS)
+  if (gf.nx % 32 == 0 && gf.ny % 8 == 0) {
+    k_mr_prolong_sep<true><<<gc_, blk, 0, c->stream>>>(c->g, gf, tables_for(mr, 0), u, c->phys.u_bot,
+                                                       c->phys.u_top, uf, kc_c);
+    k_mr_prolong_sep<true><<<gc_, blk, 0, c->stream>>>(c->g, gf, tables_for(mr, 1), v, 0.0, 0.0, vf, kc_c);
+    k_mr_prolong_sep<false><<<gf_, blk, 0, c->stream>>>(c->g, gf, tables_for(mr, 2), w, 0.0, 0.0, wf, kc_f);
+  } else {
+    k_mr_prolong<true><<<gc_, blk, 0, c->stream>>>(c->g, gf, tables_for(mr, 0), u, c->phys.u_bot,
+                                                   c->phys.u_top, uf, kc_c);
+    k_mr_prolong<true><<<gc_, blk, 0, c->stream>>>(c->g, gf, tables_for(mr, 1), v, 0.0, 0.0, vf, kc_c);
+    k_mr_prolong<false><<<gf_, blk, 0, c->stream>>>(c->g, gf, tables_for(mr, 2), w, 0.0, 0.0, wf, kc_f);
+  }
   c->launches += 3;
   return cudaGetLastError();
 }
@@ -293,12 +459,25 @@ cudaError_t scalar_substep(afid_mr* mr, int l, double dts, double* Tf) {
   }
   {
     ProfScope ps(c, KF_MR_RHS);
-    dim3 blk(32, 8);
-    const long long bpp = (long long)ceil_div(gf.nx, 32) * ceil_div(gf.ny, 8);
+    // shared-flux kernel when the blocks tile the plane exactly (no thread
+    // leaves before the per-level barrier), the plain one otherwise
+    const int wpr = gf.nx % 64 == 0 ? 2 : (gf.nx % 32 == 0 ? 1 : 0);
+    const int by = wpr == 2 ? 4 : 8;
+    const bool shared = wpr > 0 && gf.ny % by == 0;
+    const int bx = shared ? 32 * wpr : 32;
+    dim3 blk(bx, by);
+    const long long bpp = (long long)ceil_div(gf.nx, bx) * ceil_div(gf.ny, by);
     const int kc = z_chunk(c, bpp, gf.nz);
-    dim3 grd(ceil_div(gf.nx, 32), ceil_div(gf.ny, 8), ceil_div(gf.nz, kc));
-    k_mr_scalar_rhs<<<grd, blk, 0, c->stream>>>(gf, mr->mf, c->phys.kappa, l, dts, mr->uf, mr->vf, mr->wf,
-                                                Tf, mr->HT, mr->RT, mr->cntab, kc);
+    dim3 grd(ceil_div(gf.nx, bx), ceil_div(gf.ny, by), ceil_div(gf.nz, kc));
+    if (shared && wpr == 2)
+      k_mr_scalar_rhs_sh<4, 2><<<grd, blk, 0, c->stream>>>(gf, mr->mf, c->phys.kappa, l, dts, mr->uf, mr->vf,
+                                                           mr->wf, Tf, mr->HT, mr->RT, mr->cntab, kc);
+    else if (shared)
+      k_mr_scalar_rhs_sh<8, 1><<<grd, blk, 0, c->stream>>>(gf, mr->mf, c->phys.kappa, l, dts, mr->uf, mr->vf,
+                                                           mr->wf, Tf, mr->HT, mr->RT, mr->cntab, kc);
+    else
+      k_mr_scalar_rhs<<<grd, blk, 0, c->stream>>>(gf, mr->mf, c->phys.kappa, l, dts, mr->uf, mr->vf, mr->wf,
+                                                  Tf, mr->HT, mr->RT, mr->cntab, kc);
     c->launches++;
   }
   {

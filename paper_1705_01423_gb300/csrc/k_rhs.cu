@@ -34,13 +34,14 @@ struct PhysR {
   double nu, kappa, buoy, ubot, utop;
 };
 
-// WPR warps per block row: 1 (BX = min(32, nx), BY = 8) or 2 (BX = 64, BY = 4;
-// the two warps of a row pass their facing edge fluxes through shared
-// memory, so only the block's outer edges recompute neighbour fluxes).
+// WPR warps per block row: 1 (BX = min(32, nx), BY = 8; two blocks per SM) or
+// 2 (BX = 64, BY = 8, one 512-thread block per SM; the two warps of a row pass
+// their facing edge fluxes through shared memory, so only the block's outer
+// edges recompute neighbour fluxes, and 8 rows put the y edge on 1/8 of them).
 // TM: 0 no temperature, 1 temperature advanced (HT, RT written), 2 T only
 // supplies the buoyancy of the w equation (T kept on another grid).
 template <int TM, int BY, int WPR>
-__global__ void __launch_bounds__(32 * WPR * BY, 2) k_rhs_zm(Grid g, Metric m, PhysR ph, int l, double dt_in,
+__global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_zm(Grid g, Metric m, PhysR ph, int l, double dt_in,
                                                     const double* __restrict__ scal,
                                                     const double* __restrict__ u,
                                                     const double* __restrict__ v,
@@ -306,7 +307,7 @@ cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const d
   ProfScope ps(c, KF_RHS);
   const Grid& g = c->g;
   const bool wide = g.nx % 64 == 0;
-  const int BY = wide ? 4 : 8;
+  const int BY = 8;
   const int bx = wide ? 64 : x_block(g.nx, 32);
   // split the z-march into chunks so that the grid is about eight waves of
   // two resident blocks per SM (the chunk start re-reads one plane)
@@ -325,13 +326,13 @@ cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const d
                                                      Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3],         \
                                                      c->cntab, kchunk)
   if (T && HT) {
-    if (wide) AFID_RHS(1, 4, 2);
+    if (wide) AFID_RHS(1, 8, 2);
     else AFID_RHS(1, 8, 1);
   } else if (T) {
-    if (wide) AFID_RHS(2, 4, 2);
+    if (wide) AFID_RHS(2, 8, 2);
     else AFID_RHS(2, 8, 1);
   } else {
-    if (wide) AFID_RHS(0, 4, 2);
+    if (wide) AFID_RHS(0, 8, 2);
     else AFID_RHS(0, 8, 1);
   }
 #undef AFID_RHS

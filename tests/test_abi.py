@@ -97,3 +97,23 @@ def test_workspace_bytes(L):
     assert b64 > 8 * n * 5
     d2, z2 = desc(64, 32, 16, prec=1)
     assert L.afid_workspace_bytes(C.byref(d2)) > 0
+
+
+def test_refined_grid_calls_reject_null_handles(L):
+    """The afid_mr_* entry points validate on the host: a NULL context or
+    handle is refused before any CUDA call."""
+    from paper_1705_01423_gb300 import afid
+    bad = afid.AFID_ERR_INVALID_ARG
+    h = C.c_void_p(123)
+    assert L.afid_mr_create(None, 2, 2, 2, C.byref(h)) == bad
+    assert not h.value  # the out handle is cleared first
+    assert L.afid_mr_create(None, 2, 2, 2, None) == bad
+    assert L.afid_mr_destroy(None) == bad
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    assert L.afid_mr_dims(None, C.byref(a), C.byref(b), C.byref(c)) == bad
+    assert L.afid_mr_workspace_bytes(None) == 0
+    assert L.afid_mr_faces(None, None) == bad
+    assert L.afid_mr_restrict(None, None, None) == bad
+    assert L.afid_mr_prolong(None, None, None, None, None, None, None, 0.0, None, None, None) == bad
+    assert L.afid_mr_scalar_advance(None, 1e-3, 1, None, None, None, None, None, None, None) == bad
+    assert L.afid_mr_step(None, 1e-3, 1, None, None, None, None, None, None, None, None, None) == bad

@@ -59,10 +59,15 @@ def test_fine_faces(r):
     assert np.abs(m.faces() - gf.zf.numpy()).max() <= 1e-15
 
 
-@pytest.mark.parametrize("r,theta", [((1, 1, 1), 0.0), ((2, 2, 2), 0.0), ((2, 2, 2), 0.37),
-                                     ((3, 2, 1), 8.0 / 15.0), ((1, 3, 4), 1.0)])
-def test_prolong_parity(r, theta):
-    w, ctx, m, g, gf = setup("couette1024", (32, 16, 10), r)  # u wall values -1, +1
+@pytest.mark.parametrize("shape,r,theta", [((32, 16, 10), (1, 1, 1), 0.0),
+                                           ((32, 16, 10), (2, 2, 2), 0.0),
+                                           ((32, 16, 10), (2, 2, 2), 0.37),
+                                           ((32, 16, 10), (3, 2, 1), 8.0 / 15.0),
+                                           ((32, 16, 10), (1, 3, 4), 1.0),
+                                           ((32, 8, 10), (1, 1, 1), 0.0),   # 8 coarse rows, ry = 1: 9 block rows wrap
+                                           ((48, 16, 10), (1, 2, 2), 0.5)])  # 48 fine columns: per-column kernel
+def test_prolong_parity(shape, r, theta):
+    w, ctx, m, g, gf = setup("couette1024", shape, r)  # u wall values -1, +1
     vel0 = noisy_velocity(w, 1)
     vel1 = noisy_velocity(w, 2)
     out = m.prolong(tuple(gpu(a) for a in vel0), tuple(gpu(a) for a in vel1), theta)
@@ -79,9 +84,12 @@ def test_restrict_parity(r):
     assert maxrel(Tc, omr.restrict(r, Tf)) <= 1e-13
 
 
-@pytest.mark.parametrize("r,n_sub", [((2, 2, 2), 1), ((2, 2, 2), 2), ((3, 1, 2), 3)])
-def test_scalar_advance_parity(r, n_sub):
-    w, ctx, m, g, gf = setup("rb512", (32, 16, 12), r)
+@pytest.mark.parametrize("shape,r,n_sub", [((32, 16, 12), (2, 2, 2), 1),   # 64-wide shared-flux blocks
+                                           ((32, 16, 12), (2, 2, 2), 2),
+                                           ((32, 16, 12), (3, 1, 2), 3),   # 32-wide shared-flux blocks
+                                           ((48, 16, 12), (1, 1, 2), 1)])  # plain kernel (48 columns)
+def test_scalar_advance_parity(shape, r, n_sub):
+    w, ctx, m, g, gf = setup("rb512", shape, r)
     vel0 = noisy_velocity(w, 4, 0.5)
     vel1 = noisy_velocity(w, 5, 0.5)
     ph = oracle_phys(w)
