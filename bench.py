@@ -437,7 +437,7 @@ def run_ours(args):
     # ---- side measurements: Poisson solve alone, FP64 vs mixed
     extra = {}
     if not args.no_extra and rank == 0:
-        extra = side_measurements(ctx, w, dev, tma=not args.no_tma)
+        extra = side_measurements(ctx, w, dev, tma=not args.no_tma, state=S)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -482,9 +482,44 @@ def timed(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def side_measurements(ctx, w, dev, tma=True):
+def mixed_step_measurement(ctx, w, dev, state, tma=True, reps=3):
+    """The whole RK3/CN step with the mixed-precision Poisson solve (FP32
+    transforms and sweeps, FP64 residual refinement to 1e-10) against the FP64
+    step: time per step, and the relative L2 difference of every field after
+    one step of each from the same state with the same dt."""
+    import torch
+    from paper_1705_01423_gb300 import Context, Physics
+    stream = torch.cuda.current_stream()
+    ph = Physics(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, u_bot=w.u_bot, u_top=w.u_top,
+                 T_bot=w.T_bot, T_top=w.T_top)
+    mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
+                   refine_max_iter=6, phys=ph, tma=tma)
+    dt = float(w.dt_max)
+    clone = lambda xs: [x.clone() if x is not None else None for x in xs]
+    zeros = lambda xs: [torch.zeros_like(x) if x is not None else None for x in xs[:4]]
+    S64, Sm = clone(state), clone(state)
+    H64, Hm = zeros(state[:3] + [state[3]]), zeros(state[:3] + [state[3]])
+    ctx.rk3_step(S64, H64, dt)
+    mctx.rk3_step(Sm, Hm, dt)
+    torch.cuda.synchronize()
+    names = ["u", "v", "w", "T", "p"]
+    err = {n: float((a - b).norm() / max(float(b.norm()), 1e-300))
+           for n, a, b in zip(names, Sm, S64) if a is not None}
+    Sw, Hw = clone(state), zeros(state[:3] + [state[3]])
+    ms_m = timed(lambda: mctx.rk3_step(Sw, Hw, dt), reps, stream)
+    ms_64 = timed(lambda: ctx.rk3_step(Sw, Hw, dt), reps, stream)
+    mctx.close()
+    pts = w.nx * w.ny * w.nz
+    return {"ms_per_step_mixed": ms_m, "ms_per_step_fp64": ms_64, "speedup": ms_64 / ms_m,
+            "grid_points_per_s_mixed": pts / (ms_m / 1e3), "refine_tol": MIXED_TOL,
+            "rel_l2_vs_fp64_step": err, "dt": dt,
+            "note": "one step from the benchmark's state after its timed steps, fixed dt = dt_max"}
+
+
+def side_measurements(ctx, w, dev, tma=True, state=None):
     """Poisson solve alone on the same grid: FP64 direct vs mixed FP32 + FP64
-    refinement, with the mixed error against the FP64 GPU solve."""
+    refinement, with the mixed error against the FP64 GPU solve; the whole
+    step with the mixed solve; the refined temperature grid."""
     import torch
     import synth
     from paper_1705_01423_gb300 import Context
@@ -518,6 +553,11 @@ def side_measurements(ctx, w, dev, tma=True):
     ctx.profile(False)
     out["cufft_comparison"] = cufft_comparison(b, out, stream)
     del b, phi64
+    if state is not None:
+        try:
+            out["rk3_step_mixed"] = mixed_step_measurement(ctx, w, dev, state, tma=tma)
+        except Exception as e:  # report, do not hide
+            out["rk3_step_mixed"] = {"error": str(e)}
     try:
         out["multires"] = multires_measurement(ctx, w, dev)
     except Exception as e:  # report, do not hide
@@ -559,12 +599,14 @@ def multires_measurement(ctx, w, dev, r=(2, 2, 2), n_sub=1, reps=3):
     fine = m.nx * m.ny * m.nz
     nsubst = 3 * n_sub  # refined substeps per coupled step
     # FP64 operation model per fine point and substep: the temperature terms
-    # (36: face velocities 8, x/y fluxes 8, z flux 3, divergence 6, horizontal
+    # with shared face fluxes (31: own x and y face fluxes 8, the block-edge
+    # fluxes 2 + 1 (64-wide rows, 4 rows), z flux 3, divergence 6, horizontal
     # Laplacian 5, H 1, CN explicit side 3, R 2) and the prolongation (per
-    # component a z interpolation, 2, plus the bilinear value of a coarse
-    # plane, 6, shared by rz fine levels)
-    ops_rhs = 36.0 * fine * nsubst
-    ops_pro = 3 * (2.0 + 6.0 / r[2]) * fine * nsubst
+    # component a z interpolation, 2, plus per coarse plane a y interpolation,
+    # 2, and the column's share of the block's x interpolations of 8/ry + 1
+    # coarse rows, 2 (8/ry + 1) / 8, shared by rz fine levels)
+    ops_rhs = 31.0 * fine * nsubst
+    ops_pro = 3 * (2.0 + (2.0 + 2.0 * (8.0 / r[1] + 1.0) / 8.0) / r[2]) * fine * nsubst
     peak = FP64_OPS_PEAK * 1e12
     out = {"refinement": list(r), "n_sub": n_sub, "fine_grid": [m.nx, m.ny, m.nz],
            "ms_per_coupled_step": ms, "fine_grid_points_per_s": fine / (ms / 1e3),
