@@ -220,3 +220,32 @@ def test_fullsize_fourier_mode_closed_form():
     err = float((Tf[1:-1] - exact[None]).abs().max())
     assert err <= 1e-12, err
     assert float((Tf[0] - 1.0).abs().max()) == 0.0 and float(Tf[-1].abs().max()) == 0.0
+
+
+def test_refined_grid_argument_checks():
+    """Host-side validation with a live context: refinement factors outside
+    1..8, a context without the RK3 workspace, dt <= 0 and n_sub < 1 are
+    refused before anything is launched, and the context stays usable."""
+    from paper_1705_01423_gb300 import AfidError
+    from paper_1705_01423_gb300.afid import AFID_ERR_INVALID_ARG
+    w = synth.workload("rb512", nx=32, ny=16, nz=8)
+    ctx = make_ctx(w)
+    for r in [(0, 1, 1), (1, 9, 1), (2, 2, -1)]:
+        with pytest.raises(AfidError) as e:
+            MultiRes(ctx, *r)
+        assert e.value.status == AFID_ERR_INVALID_ARG
+    pctx = make_ctx(w, poisson_only=True)
+    with pytest.raises(AfidError):
+        MultiRes(pctx, 2, 2, 2)
+    m = MultiRes(ctx, 2, 2, 2)
+    z = lambda s: torch.zeros(s, dtype=torch.float64, device="cuda")
+    vel = (z(ctx.cell), z(ctx.cell), z(ctx.face))
+    Tf = z(m.fface)
+    for dt, n in [(0.0, 1), (-1e-3, 1), (1e-3, 0)]:
+        with pytest.raises(AfidError):
+            m.scalar_advance(dt, n, vel, vel, Tf)
+    with pytest.raises(ValueError):  # wrong fine shape, caught by the binding
+        m.restrict(z(ctx.face))
+    m.scalar_advance(1e-3, 1, vel, vel, Tf)  # still usable
+    torch.cuda.synchronize()
+    assert float(Tf.abs().max()) == 0.0
