@@ -155,10 +155,11 @@ struct afid_ctx {
   long long launches;
   afid::Prof* prof;
   // TMA-staged FP32 y transforms: tensor map of the spectral workspace and
-  // launch shape; tma_y = 0 when unused (FP64 contexts, ny > 512, AFID_NO_TMA)
+  // launch shape and tile width (kx columns); tma_y = 0 when unused (FP64
+  // contexts, ny not a power of two or > 2048, AFID_NO_TMA)
   CUtensorMap tmy;
   int tma_y;
-  int tmy_stages, tmy_threads, tmy_blocks_per_sm;
+  int tmy_stages, tmy_threads, tmy_blocks_per_sm, tmy_tk;
   size_t tmy_smem;
 };
 

@@ -5,11 +5,13 @@
 // The spectral array [nz][ny][P] (complex, row pitch P) is read as a 3-D
 // tensor of scalars {2 (M + 1), ny, nz}. One tile is TK consecutive kx
 // columns x all ny rows of one z plane; its box lands in shared memory as
-// rows of TK complex values (TK x element = 128 bytes), so that the TK lines
-// are transformed side by side: the lanes of a warp run along kx and every
-// Stockham access reads or writes whole 128-byte rows (no bank conflicts, no
-// padding). Columns beyond kx = M are outside the tensor: they load as zeros
-// and are not stored.
+// rows of TK complex values, so that the TK lines are transformed side by
+// side: the lanes of a warp run along kx and every Stockham access reads or
+// writes whole rows. TK = 16 (128-byte rows) up to ny = 512; beyond, TK =
+// 8192 / ny (8 at 1024, 4 at 2048: 64- and 32-byte rows, still whole DRAM
+// sectors), which keeps a stage at 64 KB and the block at ny/8 threads per
+// line = 1024. Columns beyond kx = M are outside the tensor: they load as
+// zeros and are not stored.
 //
 // A persistent block walks its tiles with a ring of S shared-memory stages:
 // while tile i is transformed, the load of tile i+1 and the store of tile i-1
@@ -30,20 +32,17 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 // plain kernel keep the FP64 pipe busier than one block of this ring (whose
 // 64 KB stages allow one block per SM at ny = 512); measured at 512 x 512 x
 // 384, 5.08 ms (plain) against 5.46 ms (ring) for the two y passes of a solve.
-template <typename R>
-struct TileK;
-// TK columns per tile (TK x complex = 128-byte rows); MAXT = TK x 512/8, the
-// block size at the largest ny served (512)
-template <> struct TileK<float> { static constexpr int TK = 16, MAXT = 1024; };
+// TK columns per tile; the block has TK x ny/8 <= 1024 threads
+constexpr int kTmaMaxThreads = 1024;
+inline int tma_tile_columns(int ny) { return ny <= 512 ? 16 : 8192 / ny; }
 
-template <typename R, bool INV>
-__global__ void __launch_bounds__(TileK<R>::MAXT, 1) k_fft_y_tma(const __grid_constant__ CUtensorMap map, Grid g,
+template <typename R, bool INV, int TK>
+__global__ void __launch_bounds__(kTmaMaxThreads, 1) k_fft_y_tma(const __grid_constant__ CUtensorMap map, Grid g,
                                                        const typename cplx<R>::T* __restrict__ tw,
                                                        const double* __restrict__ skip,
                                                        double* __restrict__ scal, int stages,
                                                        int ntile_x) {
   using C = typename cplx<R>::T;
-  constexpr int TK = TileK<R>::TK;
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int N = g.ny;
@@ -138,32 +137,39 @@ static EncodeTiledFn encode_tiled() {
 }
 
 template <typename R>
-static size_t ffty_tma_smem(const Grid& g, int stages) {
+static size_t ffty_tma_smem(const Grid& g, int TK, int stages) {
   using C = typename cplx<R>::T;
-  return (size_t)stages * TileK<R>::TK * g.ny * sizeof(C) + (size_t)g.ny * sizeof(C) + stages * sizeof(uint64_t);
+  return (size_t)stages * TK * g.ny * sizeof(C) + (size_t)g.ny * sizeof(C) + stages * sizeof(uint64_t);
+}
+
+template <bool INV>
+static void* tma_kernel(int TK) {
+  return TK == 16 ? (void*)k_fft_y_tma<float, INV, 16>
+                  : (TK == 8 ? (void*)k_fft_y_tma<float, INV, 8> : (void*)k_fft_y_tma<float, INV, 4>);
 }
 
 // Sets up the TMA y transform of a mixed-precision context when the sizes
-// allow it (ny a power of two, 16 <= ny <= 512, a tile ring of at least two stages in shared
-// memory); leaves c->tma_y = 0 (the plain kernel is used) otherwise.
+// allow it (ny a power of two, 16 <= ny <= 2048, a tile ring of at least two
+// stages in shared memory); leaves c->tma_y = 0 (the plain kernel is used)
+// otherwise.
 cudaError_t init_ffty_tma(afid_ctx* c) {
   c->tma_y = 0;
   const Grid& g = c->g;
-  if (g.ny > 512 || g.ny < 8 || (g.ny & (g.ny - 1)) != 0) return cudaSuccess;  // power-of-two ny
+  if (g.ny > 2048 || g.ny < 8 || (g.ny & (g.ny - 1)) != 0) return cudaSuccess;  // power-of-two ny
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return cudaSuccess;
   if (c->prec != AFID_MIXED) return cudaSuccess;
-  const int TK = TileK<float>::TK;
+  const int TK = tma_tile_columns(g.ny);
   const size_t csz = sizeof(float2);
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   int stages = 3;
-  auto need = [&](int s) { return ffty_tma_smem<float>(g, s); };
+  auto need = [&](int s) { return ffty_tma_smem<float>(g, TK, s); };
   // + static shared memory of the kernel (128 B)
   while (stages > 2 && need(stages) + 256 > (size_t)smem_optin) --stages;
   if (need(stages) + 256 > (size_t)smem_optin) return cudaSuccess;
   const int threads = TK * (g.ny / 8);
-  if (threads > 1024 || threads < 32) return cudaSuccess;
+  if (threads > kTmaMaxThreads || threads < 32) return cudaSuccess;
 
   cuuint64_t dims[3] = {(cuuint64_t)2 * (g.M + 1), (cuuint64_t)g.ny, (cuuint64_t)g.nz};
   cuuint64_t strides[2] = {(cuuint64_t)g.P * csz, (cuuint64_t)g.ny * g.P * csz};
@@ -176,14 +182,15 @@ cudaError_t init_ffty_tma(afid_ctx* c) {
   const size_t sm = need(stages);
   cudaError_t e;
   int per_sm = 0;
-  for (auto kf : {k_fft_y_tma<float, false>, k_fft_y_tma<float, true>})
+  for (void* kf : {tma_kernel<false>(TK), tma_kernel<true>(TK)})
     if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_y_tma<float, false>, threads, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tma_kernel<false>(TK), threads, sm);
   if (e || per_sm < 1) {
     cudaGetLastError();
     return cudaSuccess;
   }
   c->tmy_stages = stages;
+  c->tmy_tk = TK;
   c->tmy_threads = threads;
   c->tmy_smem = sm;
   c->tmy_blocks_per_sm = per_sm;
@@ -191,17 +198,23 @@ cudaError_t init_ffty_tma(afid_ctx* c) {
   return cudaSuccess;
 }
 
-template <typename R>
-cudaError_t run_fft_y_tma(afid_ctx* c, const typename cplx<R>::T* tw, bool inv, const double* skip) {
+template <typename R, int TK>
+static void launch_tma(afid_ctx* c, const typename cplx<R>::T* tw, bool inv, const double* skip) {
   const Grid& g = c->g;
-  constexpr int TK = TileK<R>::TK;
   const int ntile_x = ceil_div(g.M + 1, TK);
   const long long ntiles = (long long)ntile_x * g.nz;
   long long blocks = (long long)c->num_sms * c->tmy_blocks_per_sm;
   if (blocks > ntiles) blocks = ntiles;
-  auto kf = inv ? k_fft_y_tma<R, true> : k_fft_y_tma<R, false>;
+  auto kf = inv ? k_fft_y_tma<R, true, TK> : k_fft_y_tma<R, false, TK>;
   kf<<<(int)blocks, c->tmy_threads, c->tmy_smem, c->stream>>>(c->tmy, g, tw, skip, c->scal, c->tmy_stages,
                                                                ntile_x);
+}
+
+template <typename R>
+cudaError_t run_fft_y_tma(afid_ctx* c, const typename cplx<R>::T* tw, bool inv, const double* skip) {
+  if (c->tmy_tk == 16) launch_tma<R, 16>(c, tw, inv, skip);
+  else if (c->tmy_tk == 8) launch_tma<R, 8>(c, tw, inv, skip);
+  else launch_tma<R, 4>(c, tw, inv, skip);
   c->launches++;
   return cudaGetLastError();
 }

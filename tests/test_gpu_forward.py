@@ -271,13 +271,15 @@ def test_poisson_fp64_warp_partitioned_tridiag(shape):
 
 
 @pytest.mark.parametrize("shape", [(32, 16, 12), (64, 32, 37), (128, 64, 24), (64, 128, 19),
-                                   (64, 64, 33), (128, 32, 48), (64, 256, 9), (32, 512, 5)])
+                                   (64, 64, 33), (128, 32, 48), (64, 256, 9), (32, 512, 5),
+                                   (64, 1024, 4), (48, 2048, 3), (16, 2048, 4)])
 def test_tma_y_transform_matches_plain_kernel(shape):
     """Mixed precision: the TMA-staged FP32 y transform runs the same Stockham
     passes with the same twiddles on every line as the plain kernel, so both
     refined solves agree to round-off; both match the oracle. Shapes span one to several column tiles,
-    the zero-filled ragged last tile (M + 1 not a multiple of the tile width)
-    and ny below and at one TMA box."""
+    the zero-filled ragged last tile (M + 1 not a multiple of the tile width),
+    ny below and at one TMA box, and the narrower tiles past ny = 512 (8
+    columns at ny = 1024, 4 at 2048: several boxes of 256 rows per tile)."""
     nx, ny, nz = shape
     w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
     g = ogrid(w)
