@@ -237,7 +237,8 @@ afid_status afid_rk3_substep_adjoint(afid_ctx* ctx, int l, double dt, const doub
 typedef struct afid_mr afid_mr;
 
 /* 1 <= rx, ry, rz <= 8; the context must have the RK3 workspace (no
- * AFID_POISSON_ONLY). AFID_ERR_OOM if the fine workspace does not fit. */
+ * AFID_POISSON_ONLY). AFID_ERR_OOM if the fine workspace does not fit. The
+ * refined grid refers to its context: destroy it before the context. */
 afid_status afid_mr_create(afid_ctx* ctx, int rx, int ry, int rz, afid_mr** out);
 afid_status afid_mr_destroy(afid_mr* mr);
 afid_status afid_mr_dims(const afid_mr* mr, int* nxf, int* nyf, int* nzf);

@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -196,6 +197,7 @@ class Context:
         _check(lib().afid_create(C.byref(desc), C.byref(ph), C.c_void_p(stream.cuda_stream),
                                  C.byref(h)), "afid_create")
         self._h = h
+        self._children = weakref.WeakSet()
         self.workspace_bytes = int(lib().afid_workspace_bytes(C.byref(desc)))
 
     # shapes
@@ -208,6 +210,9 @@ class Context:
         return (self.nz + 1, self.ny, self.nx)
 
     def close(self):
+        # refined grids built on this context go first (they refer to it)
+        for child in list(getattr(self, "_children", ())):
+            child.close()
         if getattr(self, "_h", None):
             lib().afid_destroy(self._h)
             self._h = None
@@ -354,6 +359,7 @@ class MultiRes:
         h = C.c_void_p()
         _check(lib().afid_mr_create(ctx._h, self.r[0], self.r[1], self.r[2], C.byref(h)), "afid_mr_create")
         self._h = h
+        ctx._children.add(self)
         a, b, c = I(), I(), I()
         _check(lib().afid_mr_dims(h, C.byref(a), C.byref(b), C.byref(c)), "afid_mr_dims")
         self.nx, self.ny, self.nz = a.value, b.value, c.value

@@ -249,3 +249,13 @@ def test_refined_grid_argument_checks():
     m.scalar_advance(1e-3, 1, vel, vel, Tf)  # still usable
     torch.cuda.synchronize()
     assert float(Tf.abs().max()) == 0.0
+
+
+def test_context_close_releases_its_refined_grids_first():
+    w = synth.workload("rb512", nx=32, ny=16, nz=8)
+    ctx = make_ctx(w)
+    m = MultiRes(ctx, 2, 1, 2)
+    assert m.workspace_bytes > 0
+    ctx.close()          # closes m first: the refined grid refers to the context
+    assert m._h is None and ctx._h is None
+    m.close()            # no-op
