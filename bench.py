@@ -45,7 +45,7 @@ FP64_OPS_PEAK = 2 * 152 * 2.070e9 / 1e12          # 0.629 T FP64 ops/s
 MIXED_TOL = 1e-10
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -62,7 +62,7 @@ def parse():
                     help="only the refined-temperature-grid coupled step (2x2x2, afid_mr_step)")
     ap.add_argument("--grid", default=None,
                     help="override the workload's cells as NXxNYxNZ (profiling smaller cases)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload_from(args):
@@ -296,6 +296,32 @@ def run_multires_only(args):
     print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "multires": out}))
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (the whole job ends when it does)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_rate(points_per_replica: int, world: int, steps: int, ms: float) -> float:
+    """Grid points of every replica and step per second of the slowest rank."""
+    return points_per_replica * world * steps / (ms / 1e3)
+
+
+def replica_state(w, rank: int):
+    """Host fields (u, v, w, T or None, p) of one replica: the workload's start
+    state drawn with the rank as seed, so replicas solve different problems."""
+    import synth
+    if w.has_T:
+        return synth.rb_initial(w, seed=rank)
+    u0, v0, w0, p0 = synth.couette_initial(w, seed=rank)
+    return (u0, v0, w0, None, p0)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -316,11 +342,7 @@ def run_ours(args):
     ph = Physics(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, u_bot=w.u_bot, u_top=w.u_top,
                  T_bot=w.T_bot, T_top=w.T_top)
     ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), phys=ph, tma=not args.no_tma)
-    if w.has_T:
-        host = synth.rb_initial(w, seed=rank)
-    else:
-        u0, v0, w0, p0 = synth.couette_initial(w, seed=rank)
-        host = (u0, v0, w0, None, p0)
+    host = replica_state(w, rank)
     S = [torch.as_tensor(a).to(dev) if a is not None else None for a in host]
     H = [torch.zeros_like(S[0]), torch.zeros_like(S[1]), torch.zeros_like(S[2]),
          torch.zeros_like(S[3]) if S[3] is not None else None]
@@ -357,14 +379,10 @@ def run_ours(args):
     launches = ctx.kernel_launches() - l0
     fams = ctx.profile_read()
     ctx.profile(False)
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_step = ms / args.steps
     pts = w.nx * w.ny * w.nz
-    value = pts * world * args.steps / (ms / 1e3)
+    value = whole_job_rate(pts, world, args.steps, ms)
     # state sanity: still divergence free
     mdiv = float(ctx.max_divergence(S[0], S[1], S[2]))
 
@@ -426,12 +444,8 @@ def run_ours(args):
                     o_.copy_(d_, non_blocking=True)
         e3.record(stream)
         torch.cuda.synchronize()
-        ems = e2.elapsed_time(e3)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t)
-        e2e = {"value": pts * world * k2 / (ems / 1e3), "unit": "grid-points/s", "h2d_bytes_per_step": bi,
+        ems = max_over_ranks(e2.elapsed_time(e3), world, dev)
+        e2e = {"value": whole_job_rate(pts, world, k2, ems), "unit": "grid-points/s", "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bi, "steps": k2}
 
     # ---- side measurements: Poisson solve alone, FP64 vs mixed
