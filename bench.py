@@ -530,6 +530,90 @@ def mixed_step_measurement(ctx, w, dev, state, tma=True, reps=3):
             "note": "one step from the benchmark's state after its timed steps, fixed dt = dt_max"}
 
 
+def workload_measurements(dev, reps=5):
+    """The other workloads of the benchmark set, each on its own context:
+    the pressure correction on 64^3 (L2-resident and latency-bound: reported,
+    not held to a roofline), the plane Couette RK3 step at 1024x512x256 with
+    its FP64 and mixed Poisson solves, and the adjoint rollout (forward and
+    backward of dNu/dT0 over 20 steps, checkpoints every 5) at 256x256x128."""
+    import torch
+    import synth
+    from paper_1705_01423_gb300 import Context, Physics
+    from paper_1705_01423_gb300.autodiff import nusselt_gradient, _run_step
+    stream = torch.cuda.current_stream()
+    out = {}
+    phys = lambda w: Physics(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, u_bot=w.u_bot, u_top=w.u_top,
+                             T_bot=w.T_bot, T_top=w.T_top)
+    # plain FP64 pressure correction, 64^3
+    w = synth.workload("pc64")
+    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), poisson_only=True)
+    U, V, W = (torch.as_tensor(a).to(dev) for a in synth.velocity_noise(w, 0))
+    P = torch.zeros(ctx.cell, dtype=torch.float64, device=dev)
+    info = ctx.project(U, V, W, P, info=True)
+    ms = timed(lambda: ctx.project(U, V, W, P), 20, stream)
+    out["pc64_pressure_correction"] = {"ms": ms, "grid_points_per_s": w.nx * w.ny * w.nz / (ms / 1e3),
+                                       "max_div_after_first": info["max_div"]}
+    ctx.close()
+    # plane Couette, 1024 x 512 x 256: RK3 step (CFL dt on the device), FP64 and mixed solves
+    w = synth.workload("couette1024")
+    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), phys=phys(w))
+    S = [torch.as_tensor(a).to(dev) if a is not None else None for a in replica_state(w, 0)]
+    H = [torch.zeros_like(S[0]), torch.zeros_like(S[1]), torch.zeros_like(S[2]), None]
+
+    def cstep():
+        ctx.cfl(S[0], S[1], S[2], w.cfl, w.dt_max)
+        for l in range(3):
+            ctx.rk3_substep(l, -1.0, *S, *H)
+
+    for _ in range(3):
+        cstep()
+    ms = timed(cstep, reps, stream)
+    b = torch.as_tensor(synth.noise((w.nz, w.ny, w.nx), seed=7)).to(dev)
+    phi = torch.empty_like(b)
+    ms64 = timed(lambda: ctx.poisson_solve(b, phi), reps, stream)
+    mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
+                   refine_max_iter=6, poisson_only=True)
+    phim = torch.empty_like(b)
+    _, minfo = mctx.poisson_solve(b, phim, info=True)
+    msm = timed(lambda: mctx.poisson_solve(b, phim), reps, stream)
+    out["couette1024"] = {"rk3_step_ms": ms, "grid_points_per_s": w.nx * w.ny * w.nz / (ms / 1e3),
+                          "poisson_fp64_ms": ms64, "poisson_mixed_ms": msm, "mixed_speedup": ms64 / msm,
+                          "mixed_iters": minfo["iters"],
+                          "mixed_rel_l2_vs_fp64": float((phim - phi).norm() / phi.norm())}
+    mctx.close()
+    ctx.close()
+    del S, H, b, phi, phim
+    torch.cuda.empty_cache()
+    # adjoint rollout: Ra = 1e7, 256 x 256 x 128, 20 steps, checkpoints every 5
+    w = synth.workload("adj256")
+    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), phys=phys(w))
+    st = [torch.as_tensor(a).to(dev) for a in synth.rb_initial(w, 0)]
+    S = [a.clone() for a in st]
+    dts = []
+    for _ in range(w.steps):  # the rollout's dt sequence (CFL), frozen for the adjoint
+        cflm = float(ctx.cfl(S[0], S[1], S[2], w.cfl, w.dt_max))
+        dts.append(min(w.cfl / cflm, w.dt_max))
+        _run_step(ctx, dts[-1], S)
+    ra = w.extra["Ra"]
+    nusselt_gradient(ctx, st, dts, ra, 1.0, checkpoint_every=w.extra["checkpoint_every"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nu, gT = nusselt_gradient(ctx, st, dts, ra, 1.0, checkpoint_every=w.extra["checkpoint_every"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    S = [a.clone() for a in st]
+    fwd = timed(lambda: [_run_step(ctx, dt, S) for dt in dts], 1, stream)
+    out["adj256_nusselt_gradient"] = {"ms_forward_and_adjoint": ms, "ms_forward_only": fwd,
+                                      "adjoint_over_forward": ms / fwd, "steps": w.steps,
+                                      "checkpoint_every": w.extra["checkpoint_every"], "nu": nu,
+                                      "grad_max_abs": float(gT.abs().max())}
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def side_measurements(ctx, w, dev, tma=True, state=None):
     """Poisson solve alone on the same grid: FP64 direct vs mixed FP32 + FP64
     refinement, with the mixed error against the FP64 GPU solve; the whole
@@ -567,6 +651,10 @@ def side_measurements(ctx, w, dev, tma=True, state=None):
     ctx.profile(False)
     out["cufft_comparison"] = cufft_comparison(b, out, stream)
     del b, phi64
+    try:
+        out["workloads"] = workload_measurements(dev)
+    except Exception as e:  # report, do not hide
+        out["workloads"] = {"error": str(e)}
     if state is not None:
         try:
             out["rk3_step_mixed"] = mixed_step_measurement(ctx, w, dev, state, tma=tma)
