@@ -163,8 +163,8 @@ afid_status afid_max_divergence(afid_ctx* ctx, const double* u, const double* v,
                                 double* out_dev);
 
 /* Wall-normal statistics (the statistics of Sec. 3.2, accumulated only along
- * the wall-normal direction; the Nusselt number of Sec. 4 and the friction
- * velocity / friction Reynolds number of Sec. 4, Table 4).
+ * the wall-normal direction; the Nusselt number of Sec. 5 and the friction
+ * velocity / friction Reynolds number of Sec. 5, Table 4).
  * profiles (HOST, may be NULL): [nz+1][AFID_STAT_NQ] horizontal means,
  *   0 <u>  1 <v>  2 <u^2>  3 <v^2>            on cell planes k = 0..nz-1 (row nz: 0)
  *   4 <w>  5 <w^2>  6 <T>  7 <T^2>  8 <w T>   on face planes k = 0..nz (6-8: 0 without T)

@@ -20,7 +20,7 @@ computes (AFiD, arXiv 1705.01423), written in PyTorch CPU float64 ops:
                differentiation of the very same forward code
   stats.py     wall-normal statistics: horizontal means per plane, Nusselt
                numbers, wall shear stress, friction Reynolds number (Sec. 3.2,
-               Sec. 4)
+               Sec. 5)
   sampled.py   the Poisson solve at a few wavenumber pairs (large grids)
   multires.py  temperature on a refined grid with a refined time step:
                fine grid, trilinear prolongation of the velocity, restriction

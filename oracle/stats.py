@@ -1,6 +1,6 @@
 """Wall-normal statistics: horizontal (x, y) means per wall-normal plane and
 the scalars built from them (Sec. 3.2: the statistics are accumulated only
-along the wall-normal direction, a vector reduction; Sec. 4: the Nusselt
+along the wall-normal direction, a vector reduction; Sec. 5: the Nusselt
 number of Rayleigh-Benard flow, the friction velocity and friction Reynolds
 number of plane Couette flow, Table 4).
 

@@ -455,7 +455,7 @@ cudaError_t cn_sweeps_adjoint(afid_ctx* c, double* gu, double* gv, double* gw, d
 // see a constant, so the FP32 corrections' gauge round-off is removed here).
 // ---------------------------------------------------------------------------
 // Wall-normal statistics (Sec. 3.2: statistics accumulated only along the
-// wall-normal direction, a vector reduction; Sec. 4: Nusselt number, wall
+// wall-normal direction, a vector reduction; Sec. 5: Nusselt number, wall
 // shear stress and friction Reynolds number). One block per face plane
 // k = 0..nz forms the horizontal means
 //   0 <u>  1 <v>  2 <u^2>  3 <v^2>            (cell plane k < nz)
