@@ -240,4 +240,48 @@ __device__ __forceinline__ void fft_line(C* buf, int N, const C* tw, int twstrid
   fft_line_ix<INV, GEN>(buf, N, tw, twstride, t, active, PadIx{});
 }
 
+// The same transform when the thread already holds, in x[0..7], the points
+// t + r N/8 of its line (the inputs of its butterfly in the first radix-8
+// pass, which takes no twiddles): that pass runs from registers and writes
+// its outputs to the padded line, saving one shared-memory round trip; the
+// remaining passes follow as in fft_line. The arithmetic is that of
+// fft_line, in the same order. Every thread of the block calls it (barriers).
+template <bool INV, bool GEN, typename C>
+__device__ __forceinline__ void fft_line_from_regs(C* buf, int N, C* x, const C* tw, int twstride, int t,
+                                                   bool active) {
+  if (active) {
+    dft8<INV>(x);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) buf[pad8(8 * t + r)] = x[r];
+  }
+  __syncthreads();
+  int p = 8;
+  int n2 = (N & -N) / 8;
+  int rest = N / (N & -N);
+  while (n2 >= 8) {
+    stockham_pass<8, INV>(buf, N, p, tw, twstride, t, active);
+    p *= 8;
+    n2 /= 8;
+  }
+  if (n2 == 4) {
+    stockham_pass<4, INV>(buf, N, p, tw, twstride, t, active);
+    p *= 4;
+  } else if (n2 == 2) {
+    stockham_pass<2, INV>(buf, N, p, tw, twstride, t, active);
+    p *= 2;
+  }
+  if constexpr (GEN) {
+    while (rest % 3 == 0) {
+      stockham_pass<3, INV>(buf, N, p, tw, twstride, t, active);
+      p *= 3;
+      rest /= 3;
+    }
+    while (rest % 5 == 0) {
+      stockham_pass<5, INV>(buf, N, p, tw, twstride, t, active);
+      p *= 5;
+      rest /= 5;
+    }
+  }
+}
+
 }  // namespace afid

@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
   float2* stw = sm + lines * stride;  // twiddle table, nx entries
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
   float fs = 0.f, fc = 0.f, fs2 = 0.f;  // FIRST: compensated FP32 row sum, sum of squares
+  float2 zr[8];                         // FIRST: the thread's points, for the first FFT pass
   float rr = 0.f;
   unsigned long long amax = 0ull;
   int k = 0;
@@ -311,8 +312,11 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
     k = row / g.ny;
     const size_t r0 = (size_t)row * nx;
     if (MODE == R32_FIRST) {
+      // the thread's 8 points t + q T stay in registers for the first FFT pass
       const double2* s = reinterpret_cast<const double2*>(b + r0);
-      for (int n = t; n < M; n += T) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int n = t + q * T;
         const double2 x = s[n];
         const float hx = to_real<float>(x.x), hy = to_real<float>(x.y);
         // row sum of b without FP64 arithmetic: TwoSum of the FP32 heads,
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
           const unsigned long long ay = (unsigned long long)__double_as_longlong(x.y) & 0x7fffffffffffffffull;
           amax = max(amax, max(ax, ay));
         }
-        buf[pad8(n)] = make_float2(hx, hy);
+        zr[q] = make_float2(hx, hy);
       }
     } else if (MODE == R32_RESID) {
       const int j = row - k * g.ny;
@@ -415,8 +419,12 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
       }
     }
   }
-  __syncthreads();
-  fft_line<false, GEN>(buf, M, stw, 2, t, active);
+  if (MODE == R32_FIRST) {
+    fft_line_from_regs<false, GEN>(buf, M, zr, stw, 2, t, active);
+  } else {
+    __syncthreads();
+    fft_line<false, GEN>(buf, M, stw, 2, t, active);
+  }
   if (active) {
     float2* out = spec + (size_t)row * g.P;
     for (int q = t; q <= M / 2; q += T) {
