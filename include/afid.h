@@ -275,6 +275,15 @@ afid_status afid_mr_step(afid_mr* mr, double dt, int n_sub, double* u, double* v
                          double* p, double* Hu, double* Hv, double* Hw, double* Tf,
                          afid_info* info);
 
+/* Wall-normal statistics of afid_statistics on the refined grid: the coarse
+ * velocity (u, v, w, device) prolonged to the fine grid and the fine
+ * temperature Tf (device) give the profiles (HOST, may be NULL,
+ * [nzf+1][AFID_STAT_NQ]) and the scalars (HOST, may be NULL) with the fine
+ * grid's metric, e.g. the Nusselt numbers of the refined temperature. The call
+ * synchronises the context's stream. */
+afid_status afid_mr_statistics(afid_mr* mr, const double* u, const double* v, const double* w,
+                               const double* Tf, double* profiles, afid_stats* out);
+
 /* Last status text. */
 const char* afid_status_string(afid_status s);
 

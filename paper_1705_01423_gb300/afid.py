@@ -97,6 +97,7 @@ _SIGS = {
     "afid_mr_restrict": (I, [P, P, P]),
     "afid_mr_scalar_advance": (I, [P, D, I, P, P, P, P, P, P, P]),
     "afid_mr_step": (I, [P, D, I, P, P, P, P, P, P, P, P, C.POINTER(Info)]),
+    "afid_mr_statistics": (I, [P, P, P, P, P, P, P]),
 }
 KERNEL_FAMILIES = 15
 
@@ -422,6 +423,17 @@ class MultiRes:
             self._h, float(dt), int(n_sub), _ptr(u0, cc, "u0"), _ptr(v0, cc, "v0"), _ptr(w0, cf, "w0"),
             _ptr(u1, cc, "u1"), _ptr(v1, cc, "v1"), _ptr(w1, cf, "w1"), _ptr(Tf, self.fface, "Tf")),
             "afid_mr_scalar_advance")
+
+    def statistics(self, u, v, w, Tf):
+        """Wall-normal statistics on the refined grid (afid_mr_statistics):
+        (profiles [nzf+1][9] numpy, scalars dict), as Context.statistics."""
+        cc, cf = self.ctx.cell, self.ctx.face
+        prof = np.zeros((self.nz + 1, STAT_NQ), dtype=np.float64)
+        st = Stats()
+        _check(lib().afid_mr_statistics(self._h, _ptr(u, cc, "u"), _ptr(v, cc, "v"), _ptr(w, cf, "w"),
+                                        _ptr(Tf, self.fface, "Tf"), prof.ctypes.data_as(C.c_void_p),
+                                        C.byref(st)), "afid_mr_statistics")
+        return prof, {name: getattr(st, name) for name, _ in Stats._fields_}
 
     def step(self, dt, n_sub, u, v, w, p, Hu, Hv, Hw, Tf, info=False):
         """One coupled step in place (momentum on the context's grid, Tf on

@@ -197,6 +197,11 @@ cudaError_t bstats_final(afid_ctx* c);
 // Wall-normal statistics of (u, v, w, T) into c->stat_buf (profiles, then the
 // scalars of afid_stats).
 cudaError_t statistics(afid_ctx* c, const double* u, const double* v, const double* w, const double* T);
+// The same for any grid and metric (profiles [nz+1][AFID_STAT_NQ], then 8
+// scalars, into stat_buf).
+cudaError_t statistics_grid(const Grid& g, const Metric& m, const afid_phys& ph, const double* u,
+                            const double* v, const double* w, const double* T, double* stat_buf,
+                            cudaStream_t st);
 // b = D(u, v, w) / s (s from S_PROJ_S)
 cudaError_t divergence_to(afid_ctx* c, const double* u, const double* v, const double* w, double* b);
 // projection with s, beta read from S_PROJ_S / S_PROJ_BETA

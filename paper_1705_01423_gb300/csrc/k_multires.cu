@@ -51,6 +51,7 @@ struct afid_mr {
   double *u0, *v0, *w0;  // coarse velocity at the start of a coupled step
   double *ul, *vl, *wl;  // coarse velocity at an intermediate time
   double* Tc;            // restricted temperature (coarse faces)
+  double* stat_buf;      // fine-grid statistics: profiles [nzf+1][AFID_STAT_NQ], 8 scalars
   size_t bytes;
 };
 
@@ -542,7 +543,7 @@ void periodic_table(int n, int r, bool centred, int* idx, double* wt) {
 
 void free_mr(afid_mr* mr) {
   void* ps[] = {mr->metric_buf, mr->itab, mr->wtab, mr->cntab, mr->scal, mr->uf, mr->vf, mr->wf, mr->HT,
-                mr->RT, mr->u0, mr->v0, mr->w0, mr->ul, mr->vl, mr->wl, mr->Tc};
+                mr->RT, mr->u0, mr->v0, mr->w0, mr->ul, mr->vl, mr->wl, mr->Tc, mr->stat_buf};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -645,6 +646,7 @@ afid_status afid_mr_create(afid_ctx* c, int rx, int ry, int rz, afid_mr** out) {
   mr->vl = get(nc);
   mr->wl = get(nf);
   mr->Tc = get(nf);
+  mr->stat_buf = get((size_t)(gf.nz + 1) * AFID_STAT_NQ + 8);
   if (ok) {
     ok = cudaMemcpy(mr->metric_buf, flat.data(), flat.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(mr->itab, it.data(), tot * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -717,6 +719,37 @@ afid_status afid_mr_scalar_advance(afid_mr* mr, double dt, int n_sub, const doub
   afid_status st = check({u0, v0, w0, u1, v1, w1, Tf});
   if (st) return st;
   return scalar_advance(mr, dt, n_sub, u0, v0, w0, u1, v1, w1, Tf) ? AFID_ERR_CUDA : AFID_OK;
+}
+
+afid_status afid_mr_statistics(afid_mr* mr, const double* u, const double* v, const double* w,
+                               const double* Tf, double* profiles, afid_stats* out) {
+  if (!mr) return AFID_ERR_INVALID_ARG;
+  afid_status st = check({u, v, w, Tf});
+  if (st) return st;
+  afid_ctx* c = mr->c;
+  const Grid& gf = mr->gf;
+  if (prolong(mr, u, v, w, mr->uf, mr->vf, mr->wf)) return AFID_ERR_CUDA;
+  if (statistics_grid(gf, mr->mf, c->phys, mr->uf, mr->vf, mr->wf, Tf, mr->stat_buf, c->stream))
+    return AFID_ERR_CUDA;
+  c->launches += 2;
+  const size_t np = (size_t)(gf.nz + 1) * AFID_STAT_NQ;
+  double sc[8];
+  if (profiles &&
+      cudaMemcpyAsync(profiles, mr->stat_buf, np * sizeof(double), cudaMemcpyDeviceToHost, c->stream))
+    return AFID_ERR_CUDA;
+  if (cudaMemcpyAsync(sc, mr->stat_buf + np, sizeof(sc), cudaMemcpyDeviceToHost, c->stream))
+    return AFID_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream)) return AFID_ERR_CUDA;
+  if (out) {
+    out->nu_volume = sc[0];
+    out->nu_bottom = sc[1];
+    out->nu_top = sc[2];
+    out->tau_bottom = sc[3];
+    out->tau_top = sc[4];
+    out->re_tau = sc[5];
+    out->ke = sc[6];
+  }
+  return AFID_OK;
 }
 
 afid_status afid_mr_step(afid_mr* mr, double dt, int n_sub, double* u, double* v, double* w, double* p,

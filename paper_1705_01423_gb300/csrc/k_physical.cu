@@ -542,13 +542,17 @@ __global__ void k_stats_scalars(Grid g, Metric m, afid_phys ph, const double* __
   out[6] = 0.5 * (kuv + kw) / height;
 }
 
-cudaError_t statistics(afid_ctx* c, const double* u, const double* v, const double* w, const double* T) {
-  const Grid& g = c->g;
-  k_plane_stats<<<g.nz + 1, 256, 0, c->stream>>>(g, u, v, w, T, c->stat_buf);
-  k_stats_scalars<<<1, 32, 0, c->stream>>>(g, c->m, c->phys, c->stat_buf,
-                                           c->stat_buf + (size_t)(g.nz + 1) * AFID_STAT_NQ);
-  c->launches += 2;
+cudaError_t statistics_grid(const Grid& g, const Metric& m, const afid_phys& ph, const double* u,
+                            const double* v, const double* w, const double* T, double* stat_buf,
+                            cudaStream_t st) {
+  k_plane_stats<<<g.nz + 1, 256, 0, st>>>(g, u, v, w, T, stat_buf);
+  k_stats_scalars<<<1, 32, 0, st>>>(g, m, ph, stat_buf, stat_buf + (size_t)(g.nz + 1) * AFID_STAT_NQ);
   return cudaGetLastError();
+}
+
+cudaError_t statistics(afid_ctx* c, const double* u, const double* v, const double* w, const double* T) {
+  c->launches += 2;
+  return statistics_grid(c->g, c->m, c->phys, u, v, w, T, c->stat_buf, c->stream);
 }
 
 // Reduction of the per-block partials of the first mixed-precision forward

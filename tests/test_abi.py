@@ -117,3 +117,4 @@ def test_refined_grid_calls_reject_null_handles(L):
     assert L.afid_mr_prolong(None, None, None, None, None, None, None, 0.0, None, None, None) == bad
     assert L.afid_mr_scalar_advance(None, 1e-3, 1, None, None, None, None, None, None, None) == bad
     assert L.afid_mr_step(None, 1e-3, 1, None, None, None, None, None, None, None, None, None) == bad
+    assert L.afid_mr_statistics(None, None, None, None, None, None, None) == bad

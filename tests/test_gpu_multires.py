@@ -281,3 +281,37 @@ def test_ten_coupled_steps_parity():
         ref_state, ref_T = omr.step(g, gf, (2, 2, 2), ph, 5e-3, 2, ref_state, ref_T)
         errs.append(max([rel_l2(a, b) for a, b in zip(gs, ref_state)] + [rel_l2(Tg, ref_T)]))
     assert max(errs) <= 1e-12, errs
+
+
+@pytest.mark.parametrize("name,shape,r", [("rb512", (32, 16, 12), (2, 2, 2)),
+                                          ("couette1024", (32, 16, 10), (2, 1, 3))])
+def test_refined_statistics_parity(name, shape, r):
+    """afid_mr_statistics = the oracle's statistics (plane means and scalars)
+    of the prolonged velocity and the fine temperature on the fine grid."""
+    from oracle import stats as ostats
+    over = {} if name == "rb512" else dict(kappa=2e-3, T_bot=1.0, T_top=-1.0)
+    w, ctx, m, g, gf = setup(name, shape, r, **over)
+    u, v, ww = noisy_velocity(w, 31, 0.3)
+    Tf = cpu(synth.conduction_temperature(gf.zf.numpy(), gf.ny, gf.nx, w.T_bot, w.T_top, 32, amp=0.1))
+    prof, sc = m.statistics(gpu(u), gpu(v), gpu(ww), gpu(Tf))
+    velf = omr.prolong(g, gf, r, u, v, ww, w.u_bot, w.u_top)
+    ref = ostats.plane_means(gf, *velf, Tf).numpy()
+    scale = np.maximum(np.abs(ref).max(axis=0), 1e-300)
+    assert np.all(np.abs(prof - ref).max(axis=0) <= 1e-12 * scale + 1e-300)
+    rs = ostats.scalars(gf, torch.as_tensor(ref), w.nu, w.kappa, w.u_bot, w.u_top, w.T_bot, w.T_top)
+    for k, v_ in rs.items():
+        assert abs(sc[k] - v_) <= 1e-12 * max(abs(v_), 1e-30), (k, sc[k], v_)
+
+
+def test_fullsize_refined_conduction_nusselt():
+    """Conduction profile on the refined grid (temperature 1024 x 1024 x 768):
+    Nu = 1 at both walls and in the volume from the fine temperature."""
+    w, ctx, m = fullsize()
+    zf = m.faces()
+    Tf = torch.as_tensor(synth.conduction_temperature(zf, m.ny, m.nx, w.T_bot, w.T_top, 0, amp=0.0),
+                         device="cuda")
+    z = lambda s: torch.zeros(s, dtype=torch.float64, device="cuda")
+    prof, sc = m.statistics(z(ctx.cell), z(ctx.cell), z(ctx.face), Tf)
+    assert prof.shape == (m.nz + 1, 9)
+    for k in ("nu_bottom", "nu_top", "nu_volume"):
+        assert abs(sc[k] - 1.0) <= 1e-12, (k, sc[k])
