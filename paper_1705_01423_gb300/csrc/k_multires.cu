@@ -10,17 +10,23 @@
 //   k_mr_lerp        coarse velocity at the substep's start time, linear in
 //                    time between the coarse states at t and t + dt (skipped
 //                    when that time is t);
-//   k_mr_prolong     trilinear prolongation of each velocity component from
+//   k_mr_prolong_sep trilinear prolongation of each velocity component from
 //                    its coarse staggered positions to its fine ones, one
-//                    thread per fine (x, y) column walking up in z: the
-//                    bilinear value of a coarse plane is formed once and
-//                    used by every fine level between that plane and the next;
-//   k_mr_scalar_rhs  explicit terms (advection in divergence form, horizontal
-//                    diffusion) and the Crank-Nicolson right-hand side of the
-//                    temperature, the single-grid equation on the fine grid;
+//                    thread per fine (x, y) column walking up in z: a block's
+//                    x-interpolated coarse rows are formed once per coarse
+//                    plane in shared memory, and the bilinear value of a plane
+//                    serves every fine level between that plane and the next
+//                    (k_mr_prolong: the per-column form, for fine widths that
+//                    are not multiples of 32);
+//   k_mr_scalar_rhs_sh  explicit terms (advection in divergence form,
+//                    horizontal diffusion) and the Crank-Nicolson right-hand
+//                    side of the temperature, the single-grid equation on the
+//                    fine grid, with the x/y face fluxes shared between
+//                    neighbouring threads (k_mr_scalar_rhs: per column);
 //   k_cn_tables, k_cn_sweep  the fine grid's factors and the T sweep.
 // k_mr_restrict averages the fine temperature over each coarse cell's
-// horizontal extent on the coincident face plane.
+// horizontal extent on the coincident face plane; afid_mr_statistics runs the
+// wall-normal statistics on the fine grid.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
