@@ -15,6 +15,7 @@
 // (conjugated twiddles), both unnormalised.
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace afid {
 
@@ -282,6 +283,64 @@ __device__ __forceinline__ void fft_line_from_regs(C* buf, int N, C* x, const C*
       rest /= 5;
     }
   }
+}
+
+// The same transform for N a power of two, with the last pass kept in
+// registers: after it, out[q] holds point t + q N/8 of the line (q = 0..7),
+// the points the caller writes out, so the last shared-memory round trip is
+// saved. In the last pass (span p = N/R) butterfly j = t + b N/8 has k = j
+// and writes point j + r p, i.e. q = b + r 8/R. The line in shared memory is
+// left as the previous pass wrote it. The arithmetic is that of fft_line, in
+// the same order. Every thread of the block calls it (barriers).
+template <bool INV, typename C>
+__device__ __forceinline__ void fft_line_pow2_to_regs(C* buf, int N, C* out, const C* tw, int twstride,
+                                                      int t, bool active) {
+  int passes8 = 0, n2 = N;
+  while (n2 >= 8) {
+    ++passes8;
+    n2 /= 8;
+  }
+  const int last = n2 == 4 ? 4 : (n2 == 2 ? 2 : 8);  // radix of the last pass
+  if (last == 8) --passes8;
+  int p = 1;
+  for (int i = 0; i < passes8; ++i) {
+    stockham_pass<8, INV>(buf, N, p, tw, twstride, t, active);
+    p *= 8;
+  }
+  if (!active) return;
+  const int T = N / 8;
+  auto run_last = [&](auto radix_tag) {
+    constexpr int R = decltype(radix_tag)::value;
+    constexpr int B = 8 / R;
+    const int nb = N / R;
+    C x[8];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * T;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[b * R + r] = buf[pad8(j + r * nb)];
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int k = t + b * T;  // j & (p - 1) = j in the last pass
+      C* y = x + b * R;
+      if (p > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const C w = tw[r * k * twstride];
+          y[r] = INV ? cmulc(y[r], w) : cmul(y[r], w);
+        }
+      }
+      if (R == 8) dft8<INV>(y);
+      if (R == 4) dft4<INV>(y[0], y[1], y[2], y[3]);
+      if (R == 2) dft2<INV>(y[0], y[1]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) out[b + r * B] = y[r];
+    }
+  };
+  if (last == 8) run_last(std::integral_constant<int, 8>{});
+  else if (last == 4) run_last(std::integral_constant<int, 4>{});
+  else run_last(std::integral_constant<int, 2>{});
 }
 
 }  // namespace afid

@@ -519,7 +519,12 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
     }
   }
   __syncthreads();
-  fft_line<true, GEN>(buf, M, stw, 2, t, active);
+  // FP32 lines of power-of-two length keep the last FFT pass in registers:
+  // its outputs are the thread's points t + q T written out below
+  constexpr bool REGS = !GEN && std::is_same<R, float>::value;
+  C zr[8];
+  if (REGS) fft_line_pow2_to_regs<true>(buf, M, zr, stw, 2, t, active);
+  else fft_line<true, GEN>(buf, M, stw, 2, t, active);
   R d2 = (R)0, dsum = (R)0, dcomp = (R)0;
   double psum = 0.0;
   if (active) {
@@ -528,8 +533,10 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
     // MODE 1 removes the weighted mean of phi measured after the previous
     // correction (rounded to the working precision) while adding this one
     const R pm = MODE == 1 ? to_real<R>(*pmean) : (R)0;
-    for (int n = t; n < M; n += T) {
-      const C z = buf[pad8(n)];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int n = t + q * T;
+      const C z = REGS ? zr[q] : buf[pad8(n)];
       if (MODE == 0) {
         o2[n] = make_double2((double)z.x * scale, (double)z.y * scale);
       } else {
