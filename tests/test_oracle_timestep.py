@@ -210,3 +210,130 @@ def test_cfl_listing1():
     z = torch.zeros_like(u)
     assert op.cfl_number(g, z, z, torch.zeros_like(w)) == GOLD["cfl_floor"]["value"]
     assert op.cfl_dt(g, z, z, torch.zeros_like(w), 0.7, 5e-3) == 5e-3
+
+
+# explicit terms: closed forms of single Fourier modes ---------------------------------
+# Sec. 2.1 fixes the discretisation as central, second-order and conservative on the
+# staggered grid. For a single Fourier mode on the periodic directions the central
+# differences have closed forms: the second difference of cos(theta_j) is
+# -4 sin^2(dtheta/2) cos(theta_j), and the centred first difference of sin(theta_j)
+# over two spacings is cos(theta_j) sin(dtheta). The fields below make every other
+# term of H vanish exactly, so a dropped factor 1/2, a wrong sign or a wrong spacing
+# in the horizontal diffusion or in the horizontal advection fluxes fails. Together
+# with the energy identity above (the x, y and z contributions of sum W q A(q) only
+# cancel with the right relative sign and scale), they pin the z fluxes too.
+def _xy(g):
+    """x at x-faces and centres, y at y-faces and centres, shaped for broadcasting."""
+    i = torch.arange(g.nx, dtype=torch.float64)
+    j = torch.arange(g.ny, dtype=torch.float64)
+    return (i * g.dx)[None, None, :], ((i + 0.5) * g.dx)[None, None, :], \
+        (j * g.dy)[None, :, None], ((j + 0.5) * g.dy)[None, :, None]
+
+
+def _zero(g, face=False):
+    return torch.zeros(g.face_shape() if face else g.cell_shape(), dtype=torch.float64)
+
+
+def _rel(a, ref, scale):
+    return float((a - ref).abs().max()) / scale
+
+
+EXPLICIT_GRID = dict(nx=16, ny=12, nz=9, stretch=1.7, lx=2.3, ly=1.1)
+
+
+def test_explicit_horizontal_diffusion_closed_form():
+    """nu (dxx + dyy) of cos modes: Hu = -nu 4 sin^2(pi b/ny)/dy^2 u for
+    u = cos(2 pi b y/ly), Hv = -nu 4 sin^2(pi a/nx)/dx^2 v for v = cos(2 pi a x/lx),
+    and HT = -kappa (4 sin^2(pi a/nx)/dx^2 + 4 sin^2(pi b/ny)/dy^2) T; with the
+    velocity zero, Hw = buoyancy T on the interior faces."""
+    g = grid(**EXPLICIT_GRID)
+    xf, xc, yf, yc = _xy(g)
+    a, b = 3, 2
+    nu, kappa, bu = 0.013, 0.021, 0.7
+    ph = ts.Phys(nu=nu, kappa=kappa, buoyancy=bu)
+    lamx = 4.0 * math.sin(math.pi * a / g.nx) ** 2 / g.dx ** 2
+    lamy = 4.0 * math.sin(math.pi * b / g.ny) ** 2 / g.dy ** 2
+    # u varies along y only (u sits at y-centres)
+    u = torch.cos(2 * math.pi * b * yc / g.ly).expand(g.cell_shape()).clone()
+    Hu, Hv, Hw, _ = ts.explicit_terms(g, ph, u, _zero(g), _zero(g, True), None)
+    assert _rel(Hu, -nu * lamy * u, nu * lamy) < 1e-13
+    assert float(Hv.abs().max()) == 0.0 and float(Hw.abs().max()) == 0.0
+    # v varies along x only (v sits at x-centres)
+    v = torch.cos(2 * math.pi * a * xc / g.lx).expand(g.cell_shape()).clone()
+    Hu, Hv, Hw, _ = ts.explicit_terms(g, ph, _zero(g), v, _zero(g, True), None)
+    assert _rel(Hv, -nu * lamx * v, nu * lamx) < 1e-13
+    assert float(Hu.abs().max()) == 0.0 and float(Hw.abs().max()) == 0.0
+    # T on faces, a 2-D mode times a z profile, walls held at T_bot, T_top = 0
+    hz = torch.sin(math.pi * g.zf)[:, None, None]
+    T = hz * torch.cos(2 * math.pi * a * xc / g.lx) * torch.cos(2 * math.pi * b * yc / g.ly)
+    T[0] = 0.0
+    T[-1] = 0.0
+    Hu, Hv, Hw, HT = ts.explicit_terms(g, ph, _zero(g), _zero(g), _zero(g, True), T)
+    lam = lamx + lamy
+    assert _rel(HT[1:-1], -kappa * lam * T[1:-1], kappa * lam) < 1e-13
+    assert float(HT[0].abs().max()) == 0.0 and float(HT[-1].abs().max()) == 0.0
+    assert _rel(Hw[1:-1], bu * T[1:-1], bu) < 1e-15
+    assert float(Hu.abs().max()) == 0.0 and float(Hv.abs().max()) == 0.0
+
+
+def test_explicit_advection_of_v_by_uniform_u():
+    """v = eps sin(2 pi a x/lx) carried by a uniform u = U (w = 0, solenoidal):
+    Hv = -U (v_{i+1} - v_{i-1})/(2 dx) = -U eps cos(2 pi a x/lx) sin(2 pi a/nx)/dx,
+    and Hu = 0 (u is uniform, v does not vary along y)."""
+    g = grid(**EXPLICIT_GRID)
+    xf, xc, yf, yc = _xy(g)
+    a, U, eps = 3, 0.8, 0.05
+    ph = ts.Phys()
+    v = (eps * torch.sin(2 * math.pi * a * xc / g.lx)).expand(g.cell_shape()).clone()
+    u = torch.full(g.cell_shape(), U, dtype=torch.float64)
+    Hu, Hv, Hw, _ = ts.explicit_terms(g, ph, u, v, _zero(g, True), None)
+    ref = -U * eps * torch.cos(2 * math.pi * a * xc / g.lx) * math.sin(2 * math.pi * a / g.nx) / g.dx
+    scale = U * eps / g.dx
+    assert _rel(Hv, ref.expand(g.cell_shape()), scale) < 1e-13
+    assert float(Hu.abs().max()) < 1e-15 * scale
+    assert float(Hw.abs().max()) == 0.0
+    # the closed form is not trivially small
+    assert float(ref.abs().max()) > 0.5 * U * eps * math.sin(2 * math.pi * a / g.nx) / g.dx
+
+
+def test_explicit_advection_of_u_by_uniform_v():
+    """u = eps sin(2 pi b y/ly) carried by a uniform v = V (w = 0, solenoidal):
+    Hu = -V (u_{j+1} - u_{j-1})/(2 dy) = -V eps cos(2 pi b y/ly) sin(2 pi b/ny)/dy,
+    and Hv = 0."""
+    g = grid(**EXPLICIT_GRID)
+    xf, xc, yf, yc = _xy(g)
+    b, V, eps = 2, -0.6, 0.05
+    ph = ts.Phys()
+    u = (eps * torch.sin(2 * math.pi * b * yc / g.ly)).expand(g.cell_shape()).clone()
+    v = torch.full(g.cell_shape(), V, dtype=torch.float64)
+    Hu, Hv, Hw, _ = ts.explicit_terms(g, ph, u, v, _zero(g, True), None)
+    ref = -V * eps * torch.cos(2 * math.pi * b * yc / g.ly) * math.sin(2 * math.pi * b / g.ny) / g.dy
+    scale = abs(V) * eps / g.dy
+    assert _rel(Hu, ref.expand(g.cell_shape()), scale) < 1e-13
+    assert float(Hv.abs().max()) < 1e-15 * scale
+    assert float(Hw.abs().max()) == 0.0
+
+
+def test_explicit_advection_of_face_scalar_by_uniform_flow():
+    """T = eps h(z) sin(theta), theta = 2 pi (a x/lx + b y/ly), carried by a
+    uniform (U, V) (w = 0): the volume-weighted interpolation reproduces U and V
+    on the z-faces, so HT = -eps h(z) cos(theta) (U sin(2 pi a/nx)/dx
+    + V sin(2 pi b/ny)/dy) on the interior faces, zero on the walls; the same
+    horizontal fluxes serve w."""
+    g = grid(**EXPLICIT_GRID)
+    xf, xc, yf, yc = _xy(g)
+    a, b, U, V, eps = 2, 3, 0.8, -0.6, 0.05
+    ph = ts.Phys()
+    hz = (1.0 + g.zf)[:, None, None]
+    th = 2 * math.pi * (a * xc / g.lx + b * yc / g.ly)
+    T = eps * hz * torch.sin(th)
+    T[0] = 0.0
+    T[-1] = 0.0
+    u = torch.full(g.cell_shape(), U, dtype=torch.float64)
+    v = torch.full(g.cell_shape(), V, dtype=torch.float64)
+    _, _, _, HT = ts.explicit_terms(g, ph, u, v, _zero(g, True), T)
+    ref = -eps * hz * torch.cos(th) * (U * math.sin(2 * math.pi * a / g.nx) / g.dx
+                                       + V * math.sin(2 * math.pi * b / g.ny) / g.dy)
+    scale = eps * (abs(U) / g.dx + abs(V) / g.dy) * 2.0
+    assert _rel(HT[1:-1], ref[1:-1], scale) < 1e-13
+    assert float(HT[0].abs().max()) == 0.0 and float(HT[-1].abs().max()) == 0.0
