@@ -34,12 +34,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# FP64 issue rate of this part: 2 FP64 operations (add, multiply or fused
-# multiply-add alike) per clock per SM -- an FMA-chain probe measured 1.19
-# TFLOP/s (FMA = 2 flops) at 1995 MHz on 152 SMs -- at the 2070 MHz maximum
-# SM clock. The ALU roofline below counts FP64 operations, each add, multiply
-# or FMA once, against this issue rate.
-FP64_OPS_PEAK = 2 * 152 * 2.070e9 / 1e12          # 0.629 T FP64 ops/s
+# Nominal FP64 issue rate of this part, for context only: 2 FP64 operations
+# (add, multiply or fused multiply-add alike) per clock per SM x 152 SMs x the
+# 2070 MHz maximum SM clock. The ALU roofline of the FP64 kernels uses the rate
+# measured in the same run by afid_probe_fp64_rate (FMA chains, an FMA counted
+# as one operation), each add, multiply or FMA of a kernel's formulation
+# counted once against it.
+FP64_OPS_NOMINAL = 2 * 152 * 2.070e9 / 1e12          # 0.629 T FP64 ops/s
 # The mixed-precision solve is measured at the accuracy it is held to: a
 # relative error of 1e-10 against the FP64 solve (its stopping rule's target).
 MIXED_TOL = 1e-10
@@ -292,7 +293,8 @@ def run_multires_only(args):
     ph = Physics(nu=w.nu, kappa=w.kappa, buoyancy=w.buoyancy, u_bot=w.u_bot, u_top=w.u_top,
                  T_bot=w.T_bot, T_top=w.T_top)
     ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), phys=ph)
-    out = multires_measurement(ctx, w, dev)
+    peak, _ = fp64_probe(ctx, 0)
+    out = multires_measurement(ctx, w, dev, fp64_peak=peak)
     print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "multires": out}))
 
 
@@ -360,6 +362,7 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    fp64_peak, probe = fp64_probe(ctx, local)
     ctx.profile(True)
     ctx.profile_read()
     barrier()
@@ -393,14 +396,17 @@ def run_ours(args):
     per_launch_ms = tms / max(tn, 1)
     bytes_, ops = family_work(top, w)
     t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
-    t_alu = ops / (FP64_OPS_PEAK * 1e12)
+    t_alu = ops / (fp64_peak * 1e12)
     if t_alu > t_hbm:
         ach = ops / (per_launch_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_OPS_PEAK, "unit": "TFLOP/s",
-                "frac": ach / FP64_OPS_PEAK, "traffic": traffic_for(top, w),
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": traffic_for(top, w),
                 "kernel": top, "launch_ms": per_launch_ms,
-                "peak_source": "derived FP64 issue rate: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz (FMA-chain "
-                               "probe: 1.19 TFLOP/s at 1995 MHz); FLOP here = one FP64 add, mul or FMA",
+                "peak_source": "measured in this run: afid_probe_fp64_rate (independent FP64 FMA chains, "
+                               "FMA = 1 operation), best of %d launches at a median SM clock of %s MHz; "
+                               "FLOP here = one FP64 add, mul or FMA of the kernel's formulation"
+                               % (probe["launches"], probe["sm_mhz"]),
+                "peak_nominal": FP64_OPS_NOMINAL, "fp64_probe": probe,
                 "hbm_gbs_algorithmic": bytes_ / (per_launch_ms / 1e3) / 1e9,
                 "hbm_frac_of_measured": (bytes_ / (per_launch_ms / 1e3) / 1e9) / peaks["hbm_gbs"]}
     else:
@@ -418,7 +424,7 @@ def run_ours(args):
         fw = family_work(f, w)
         if fw:
             t = v[0] / v[1] / 1e3
-            e["fp64_ops_frac"] = fw[1] / t / 1e12 / FP64_OPS_PEAK
+            e["fp64_ops_frac"] = fw[1] / t / 1e12 / fp64_peak
             e["hbm_frac_algorithmic"] = fw[0] / t / 1e9 / peaks["hbm_gbs"]
         fam_report[f] = e
 
@@ -505,7 +511,18 @@ def run_ours(args):
     # ---- side measurements: Poisson solve alone, FP64 vs mixed
     extra = {}
     if not args.no_extra and rank == 0:
-        extra = side_measurements(ctx, w, dev, tma=not args.no_tma, state=S)
+        extra = side_measurements(ctx, w, dev, tma=not args.no_tma, state=S, fp64_peak=fp64_peak)
+
+    # ---- the large mixed-precision Poisson solve (2048 x 2048 x 1024), after
+    # the step's context and fields are released (it needs about 255 GB)
+    if not args.no_extra and rank == 0:
+        ctx.close()
+        del S, H
+        torch.cuda.empty_cache()
+        try:
+            extra["poisson2048"] = poisson2048_measurement(dev)
+        except Exception as e:  # report, do not hide
+            extra["poisson2048"] = {"error": str(e)}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -536,6 +553,108 @@ def run_ours(args):
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def fp64_probe(ctx, gpu_index, launches=12, iters=20000):
+    """The FP64 rate this GPU delivers (afid_probe_fp64_rate), best of
+    `launches` timed launches, with the SM clock sampled meanwhile: the peak
+    of the ALU roofline, in T FP64 operations per second."""
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    rates = [ctx.probe_fp64_rate(iters) for _ in range(launches)]
+    c = clk.stop()
+    best = max(r for r, _ in rates)
+    return best / 1e12, {"ops_per_s": best, "launches": launches, "ms_per_launch": min(m for _, m in rates),
+                         "sm_mhz": c["sm_mhz"], "reasons": c["reasons"],
+                         "per_clock_per_sm": (best / (c["sm_mhz"] * 1e6 * 152)) if c["sm_mhz"] else None}
+
+
+def poisson2048_measurement(dev, reps=3):
+    """The large mixed-precision Poisson solve: 2048 x 2048 x 1024 cells,
+    tanh-stretched z, rhs = seeded N(0,1) noise + 8 manufactured modes
+    cos(2 pi a x) cos(2 pi b y) cos(pi m z). FP64 direct solve and mixed FP32
+    solve with FP64 refinement to 1e-10, their times and speedup; the errors of
+    both against the sampled-mode FP64 oracle (16 (kx, ky) columns: the 8
+    manufactured pairs, (0,0), the lowest and Nyquist pairs, seeded others; a
+    direct DFT of the whole rhs and FP64 Thomas per column), of the mixed
+    solve against the FP64 solve, and of the modes-only solve against the
+    continuum closed form -sum cos cos cos / (4 pi^2 (a^2 + b^2) + pi^2 m^2)
+    (the second-order discretisation error)."""
+    import numpy as np
+    import torch
+    import synth
+    from oracle import Grid, sampled
+    from paper_1705_01423_gb300 import Context
+    w = synth.workload("poisson2048")
+    free, _ = torch.cuda.mem_get_info()
+    need = 255e9
+    if free < need:
+        return {"skipped": "needs about %.0f GB of free device memory, %.0f GB free" % (need / 1e9, free / 1e9)}
+    stream = torch.cuda.current_stream()
+    g = Grid(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces())
+    t0 = time.perf_counter()
+    bh, modes = synth.manufactured_rhs(w, seed=0)
+    B = torch.from_numpy(bh).to(dev)
+    t_gen = time.perf_counter() - t0
+    pairs = [(a, b) for a, b, _ in modes]
+    for p in sampled.default_pairs(g, seed=2, count=10):
+        if p not in pairs:
+            pairs.append(p)
+    t0 = time.perf_counter()
+    ref = sampled.solve_modes(g, bh, pairs)
+    t_oracle = time.perf_counter() - t0
+    del bh
+
+    def sampled_err(phi):
+        got = sampled.mode_columns(g, phi, pairs)
+        num = sum(np.linalg.norm(got[p] - ref[p]) ** 2 for p in pairs)
+        den = sum(np.linalg.norm(ref[p]) ** 2 for p in pairs)
+        return math.sqrt(num / den)
+
+    pts = w.nx * w.ny * w.nz
+    ctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), poisson_only=True)
+    phi64 = torch.empty_like(B)
+    ms64 = timed(lambda: ctx.poisson_solve(B, phi64), reps, stream)
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    err64 = sampled_err(phi64)
+    mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
+                   refine_max_iter=6, poisson_only=True)
+    phim = torch.empty_like(B)
+    _, info = mctx.poisson_solve(B, phim, info=True)
+    msm = timed(lambda: mctx.poisson_solve(B, phim), reps, stream)
+    errm = sampled_err(phim)
+    err_m64 = float((phim - phi64).norm() / phi64.norm())
+    del phi64
+    torch.cuda.empty_cache()
+    # modes only (deterministic cosines built on the device), against the closed form
+    zc = torch.as_tensor(g.zc.numpy(), device=dev)
+    xc = (torch.arange(w.nx, device=dev, dtype=torch.float64) + 0.5) * (w.lx / w.nx)
+    yc = (torch.arange(w.ny, device=dev, dtype=torch.float64) + 0.5) * (w.ly / w.ny)
+    B.zero_()
+    for a, b, m in modes:
+        B += (torch.cos(math.pi * m * zc)[:, None, None] * torch.cos(2 * math.pi * b * yc / w.ly)[None, :, None]
+              * torch.cos(2 * math.pi * a * xc / w.lx)[None, None, :])
+    mctx.poisson_solve(B, phim)
+    exact = B
+    exact.zero_()
+    for a, b, m in modes:
+        lam = 4 * math.pi ** 2 * (a ** 2 / w.lx ** 2 + b ** 2 / w.ly ** 2) + math.pi ** 2 * m ** 2
+        exact -= (torch.cos(math.pi * m * zc)[:, None, None] * torch.cos(2 * math.pi * b * yc / w.ly)[None, :, None]
+                  * torch.cos(2 * math.pi * a * xc / w.lx)[None, None, :]) / lam
+    dzc = torch.as_tensor(g.dzc.numpy(), device=dev)[:, None, None]
+    exact -= float((dzc * exact).sum() / (dzc.sum() * w.nx * w.ny))
+    err_closed = float((phim - exact).norm() / exact.norm())
+    mctx.close()
+    del mctx, B, phim, exact
+    torch.cuda.empty_cache()
+    return {"grid": [w.nx, w.ny, w.nz], "fp64_ms": ms64, "mixed_ms": msm, "speedup": ms64 / msm,
+            "fp64_grid_points_per_s": pts / (ms64 / 1e3), "mixed_grid_points_per_s": pts / (msm / 1e3),
+            "mixed_iters": info["iters"], "refine_tol": MIXED_TOL, "err_estimate": info["err_estimate"],
+            "fp64_rel_l2_vs_sampled_oracle": err64, "mixed_rel_l2_vs_sampled_oracle": errm,
+            "mixed_rel_l2_vs_fp64_gpu": err_m64, "modes_only_rel_l2_vs_closed_form": err_closed,
+            "sampled_pairs": len(pairs), "host_rhs_generation_s": t_gen, "sampled_oracle_s": t_oracle}
 
 
 def timed(fn, reps, stream):
@@ -670,7 +789,7 @@ def workload_measurements(dev, reps=5):
     return out
 
 
-def side_measurements(ctx, w, dev, tma=True, state=None):
+def side_measurements(ctx, w, dev, tma=True, state=None, fp64_peak=FP64_OPS_NOMINAL):
     """Poisson solve alone on the same grid: FP64 direct vs mixed FP32 + FP64
     refinement, with the mixed error against the FP64 GPU solve; the whole
     step with the mixed solve; the refined temperature grid."""
@@ -717,13 +836,13 @@ def side_measurements(ctx, w, dev, tma=True, state=None):
         except Exception as e:  # report, do not hide
             out["rk3_step_mixed"] = {"error": str(e)}
     try:
-        out["multires"] = multires_measurement(ctx, w, dev)
+        out["multires"] = multires_measurement(ctx, w, dev, fp64_peak=fp64_peak)
     except Exception as e:  # report, do not hide
         out["multires"] = {"error": str(e)}
     return out
 
 
-def multires_measurement(ctx, w, dev, r=(2, 2, 2), n_sub=1, reps=3):
+def multires_measurement(ctx, w, dev, r=(2, 2, 2), n_sub=1, reps=3, fp64_peak=FP64_OPS_NOMINAL):
     """Coupled step with the temperature on a grid refined r times (afid_mr_step):
     the momentum step on the workload's grid with the restricted buoyancy, then
     n_sub refined RK3/CN temperature steps on the fine grid."""
@@ -765,7 +884,7 @@ def multires_measurement(ctx, w, dev, r=(2, 2, 2), n_sub=1, reps=3):
     # coarse rows, 2 (8/ry + 1) / 8, shared by rz fine levels)
     ops_rhs = 31.0 * fine * nsubst
     ops_pro = 3 * (2.0 + (2.0 + 2.0 * (8.0 / r[1] + 1.0) / 8.0) / r[2]) * fine * nsubst
-    peak = FP64_OPS_PEAK * 1e12
+    peak = fp64_peak * 1e12
     out = {"refinement": list(r), "n_sub": n_sub, "fine_grid": [m.nx, m.ny, m.nz],
            "ms_per_coupled_step": ms, "fine_grid_points_per_s": fine / (ms / 1e3),
            "kernel_launches_per_step": launches, "families_ms": fams,

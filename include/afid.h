@@ -190,6 +190,19 @@ typedef struct {
 afid_status afid_statistics(afid_ctx* ctx, const double* u, const double* v, const double* w,
                             const double* T, double* profiles, afid_stats* out);
 
+/* Volume-averaged Nusselt number, the objective of the adjoint rollout (the
+ * Nusselt number of Sec. 5, Table 3, in its volume form):
+ *   Nu = 1 + coef <w T>_V,  <w T>_V = sum over interior z-faces k = 1..nz-1 of
+ *        dx dy dzf_k w T / V,  V = lx ly (zf[nz] - zf[0]),
+ * coef = sqrt(Ra Pr) in free-fall units (1/kappa). w, T: device [nz+1][ny][nx].
+ * gw, gT (device [nz+1][ny][nx], either may be NULL): set to the derivatives
+ * dNu/dw = coef dx dy dzf_k T / V and dNu/dT = coef dx dy dzf_k w / V on the
+ * interior faces and zero on the walls -- the cotangent seeds of the adjoint.
+ * nu_out (HOST, may be NULL): Nu; when given, the call synchronises the
+ * context's stream. The sums are FP64 in a fixed order (deterministic). */
+afid_status afid_nusselt(afid_ctx* ctx, const double* w, const double* T, double coef,
+                         double* nu_out, double* gw, double* gT);
+
 /* Transpose of the linear map rhs -> phi of afid_poisson_solve (exact
  * transpose: grhs = W_c solve(W_c^-1 gphi), W_c the cell volumes). gphi and
  * grhs: device [nz][ny][nx]; may alias. Always FP64. */
@@ -284,6 +297,30 @@ afid_status afid_mr_step(afid_mr* mr, double dt, int n_sub, double* u, double* v
 afid_status afid_mr_statistics(afid_mr* mr, const double* u, const double* v, const double* w,
                                const double* Tf, double* profiles, afid_stats* out);
 
+/* Instrumentation: the FP64 operation rate this GPU delivers, measured. Every
+ * FP64 stage of the path is bound by FP64 instruction issue on this part, so
+ * this rate is the roofline denominator of those kernels. A kernel of
+ * independent chains of dependent FP64 fused multiply-adds (eight per thread,
+ * two 256-thread blocks per SM, `iters` FMAs per chain) runs on the context's
+ * stream after a short warm-up launch and is timed with CUDA events; an FMA
+ * counts as one operation. ops_per_s (HOST): FP64 operations per second;
+ * ms_out (HOST, may be NULL): the timed launch in milliseconds. Synchronises
+ * the stream. iters >= 1 (20000 runs about 20 ms on one GB300). */
+afid_status afid_probe_fp64_rate(afid_ctx* ctx, int iters, double* ops_per_s, double* ms_out);
+
+/* Test of the timeout path of the bounded device-side waits (the only waits
+ * in this library: the TMA tile loads of the FP32 y transform). After this
+ * call, the next TMA y-transform launch on the context runs block 0 with its
+ * first tile stage armed for the tile's bytes but no copy issued, and a 1 ms
+ * limit instead of 2 s: the block's wait runs out with nothing in flight for
+ * that stage, it sets the fault flag, waits (bounded) for its other loads and
+ * returns -- no fault and no hang. The next call that fills afid_info returns
+ * AFID_ERR_TIMEOUT (the results of that solve are not valid) and clears the
+ * flag; later calls on the context are unaffected. AFID_ERR_INVALID_ARG if the
+ * context runs no TMA transform (FP64 contexts, AFID_NO_TMA, ny not a power of
+ * two or > 2048). */
+afid_status afid_test_tma_timeout(afid_ctx* ctx);
+
 /* Last status text. */
 const char* afid_status_string(afid_status s);
 
@@ -316,19 +353,26 @@ const char* afid_kernel_family_name(int family);
  * every piece of workspace -- metric, twiddles, wavenumbers, Thomas pivot
  * table and the spectral array -- lives in one file-scope __device__ array of
  * AFID_NOALLOC_BYTES (16 MiB) that every GPU loading the library holds until
- * the process exits. The workspace needed is about
- *   16 nz ny roundup16(nx/2+1) + 8 nz (ny/2+1)(nx/2+1) bytes (+ small tables),
- * e.g. 64^3 or 128 x 128 x 64 fit; nx and ny must be powers of two here; a
- * grid that does not fit or is not of that form returns
+ * the process exits. The rule is the byte count: the grid is accepted when
+ *   16 nz ny roundup16(nx/2+1) + 8 nz (ny/2+1)(nx/2+1) bytes (the spectral
+ *   array and the pivot table, each rounded up to 256 B) + the small tables
+ *   (13 (nz+1) + 2 nx + 2 ny + nx/2 + ny/2 + 22 doubles, each rounded up to 256 B)
+ * fit in AFID_NOALLOC_BYTES; e.g. 64^3, 128 x 128 x 64 and 128 x 128 x 80
+ * fit, 256^3 does not. nx and ny must be powers of two here; a grid that does
+ * not fit or is not of that form returns
  * AFID_ERR_UNSUPPORTED_SIZE before anything is launched. The caller passes
  * the input rhs and the output phi (device, [nz][ny][nx], 16-byte aligned; they
  * may alias) and a cudaStream_t. The call uploads the tables from a static
  * host staging buffer and launches on `stream`; it calls no cudaMalloc,
- * cudaFree or other allocating routine. The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current:
- * make that first call before any stream capture. All calls share the one
- * array and its contents persist from the last call; calls that overlap on the
- * GPU (two streams, two host threads) race on it. */
+ * cudaFree or other allocating routine. Every call looks up the array's device
+ * address (cudaGetSymbolAddress, which allocates nothing) for the device and
+ * context current at that call, so a context change or a cudaDeviceReset
+ * between calls leaves no stale address behind. The first call on a device
+ * also loads the library's device code there: make that first call before
+ * any stream capture. All calls share the one array and its contents persist
+ * from the last call (every call rewrites the tables and the spectral array it
+ * uses before reading them); calls that overlap on the GPU (two streams, two
+ * host threads whose launches interleave) race on it. */
 #define AFID_NOALLOC_BYTES (16u << 20)
 afid_status afid_poisson_solve_noalloc(int nx, int ny, int nz, double lx, double ly,
                                        const double* zf_host, const double* rhs, double* phi,

@@ -79,6 +79,9 @@ _SIGS = {
     "afid_rk3_substep": (I, [P, I, D, P, P, P, P, P, P, P, P, P, C.POINTER(Info)]),
     "afid_max_divergence": (I, [P, P, P, P, P]),
     "afid_statistics": (I, [P, P, P, P, P, P, P]),
+    "afid_nusselt": (I, [P, P, P, D, C.POINTER(C.c_double), P, P]),
+    "afid_probe_fp64_rate": (I, [P, I, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "afid_test_tma_timeout": (I, [P]),
     "afid_poisson_solve_adjoint": (I, [P, P, P]),
     "afid_project_adjoint": (I, [P, P, P, P, P, D, D]),
     "afid_rk3_substep_adjoint": (I, [P, I, D, P, P, P, P, P, P, P, P, P, P, P, P, P]),
@@ -231,6 +234,14 @@ class Context:
     def kernel_launches(self) -> int:
         return int(lib().afid_kernel_launches(self._h))
 
+    def probe_fp64_rate(self, iters=20000):
+        """(FP64 operations per second, ms) of the FMA-chain probe
+        (afid_probe_fp64_rate); an FMA counts as one operation."""
+        r, ms = C.c_double(), C.c_double()
+        _check(lib().afid_probe_fp64_rate(self._h, int(iters), C.byref(r), C.byref(ms)),
+               "afid_probe_fp64_rate")
+        return r.value, ms.value
+
     def profile(self, on=True):
         _check(lib().afid_profile_enable(self._h, 1 if on else 0), "afid_profile_enable")
 
@@ -300,6 +311,18 @@ class Context:
                                      _ptr(T, self.face, "T") if T is not None else None,
                                      prof.ctypes.data_as(C.c_void_p), C.byref(st)), "afid_statistics")
         return prof, {name: getattr(st, name) for name, _ in Stats._fields_}
+
+    def nusselt(self, w, T, coef, seeds=False):
+        """Volume Nusselt number 1 + coef <w T>_V (afid_nusselt; coef = sqrt(Ra Pr)).
+        With seeds=True also returns (dNu/dw, dNu/dT) as new device tensors."""
+        import torch
+        nu = C.c_double()
+        gw = torch.empty_like(w) if seeds else None
+        gT = torch.empty_like(T) if seeds else None
+        _check(lib().afid_nusselt(self._h, _ptr(w, self.face, "w"), _ptr(T, self.face, "T"),
+                                  float(coef), C.byref(nu), _ptr(gw, self.face, "gw"),
+                                  _ptr(gT, self.face, "gT")), "afid_nusselt")
+        return (nu.value, gw, gT) if seeds else nu.value
 
     def rk3_substep(self, l, dt, u, v, w, T, p, Hu, Hv, Hw, HT, info=False):
         """dt <= 0 uses the dt set by the last cfl() call (device resident)."""

@@ -10,7 +10,8 @@ sequence forward and reuses it backward.
 
 Nu = 1 + sqrt(Ra Pr) <w T>_V, the volume form of the Nusselt number (wall
 temperatures fixed, so <-dT/dz>_V = 1), with <.>_V the sum over interior
-z-faces weighted by dx dy dzf_k divided by the box volume.
+z-faces weighted by dx dy dzf_k divided by the box volume; afid_nusselt forms
+it and its derivatives with respect to w and T on the device.
 """
 from __future__ import annotations
 
@@ -98,24 +99,10 @@ class RK3StepFn(torch.autograd.Function):
         return (None, None, G[0], G[1], G[2], G[3], G[4])
 
 
-def nusselt(ctx: Context, w, T, ra: float, pr: float, wf: torch.Tensor):
-    """Nu = 1 + sqrt(Ra Pr) sum_f W_f w T / V (wf: face weights [nz+1], zero on walls)."""
-    vol = ctx.lx * ctx.ly * 1.0
-    return 1.0 + math.sqrt(ra * pr) * float((wf[:, None, None] * w * T).sum()) / vol
-
-
-def face_weights(ctx: Context, device):
-    zf = torch.as_tensor(ctx._zf, dtype=torch.float64)
-    zc = 0.5 * (zf[1:] + zf[:-1])
-    dzf = torch.zeros(ctx.nz + 1, dtype=torch.float64)
-    dzf[1:-1] = zc[1:] - zc[:-1]
-    dx, dy = ctx.lx / ctx.nx, ctx.ly / ctx.ny
-    return (dx * dy * dzf).to(device)
-
-
 def nusselt_gradient(ctx: Context, state0, dts, ra: float, pr: float, checkpoint_every: int = 5):
     """Nu after len(dts) RK3 steps from state0 = (u, v, w, T, p) (device tensors,
-    unchanged) and dNu/dT0 (interior faces; walls are data and get zero).
+    unchanged) and dNu/dT0 (interior faces; walls are data and get zero). Nu and
+    its seed cotangents come from afid_nusselt.
 
     Checkpointing: the forward keeps the state at every `checkpoint_every`-th
     step; the backward recomputes each segment from its checkpoint, keeping the
@@ -130,12 +117,8 @@ def nusselt_gradient(ctx: Context, state0, dts, ra: float, pr: float, checkpoint
         if s % c == 0:
             ckpt[s] = _clone(S)
         _run_step(ctx, dts[s], S)
-    wf = face_weights(ctx, S[0].device)
-    nu = nusselt(ctx, S[2], S[3], ra, pr, wf)
-    coef = math.sqrt(ra * pr) / (ctx.lx * ctx.ly)
     G = _zeros_like_state(S)
-    G[2] = coef * wf[:, None, None] * S[3]          # dNu/dw
-    G[3] = coef * wf[:, None, None] * S[2]          # dNu/dT
+    nu, G[2], G[3] = ctx.nusselt(S[2], S[3], math.sqrt(ra * pr), seeds=True)  # Nu, dNu/dw, dNu/dT
     starts = sorted(ckpt)
     for seg_start in reversed(starts):
         seg_end = min(seg_start + c, n)
@@ -143,7 +126,4 @@ def nusselt_gradient(ctx: Context, state0, dts, ra: float, pr: float, checkpoint
         subs = [_run_step(ctx, dts[s], X, save_substeps=True) for s in range(seg_start, seg_end)]
         for s in reversed(range(seg_start, seg_end)):
             _step_adjoint(ctx, dts[s], subs[s - seg_start], G)
-    gT0 = G[3]
-    gT0[0] = 0.0
-    gT0[-1] = 0.0
-    return nu, gT0
+    return nu, G[3]   # the substep adjoint leaves the wall planes of gT at zero

@@ -12,11 +12,12 @@ using namespace afid;
 
 namespace afid {
 
-void metric_host(int nz, double rdx2, double rdy2, const double* zf, std::vector<double>& flat,
-                 std::vector<size_t>& offs) {
-  std::vector<double> dzc(nz), rdzc(nz), dzf(nz + 1), rdzf(nz + 1), pa(nz, 0.0), pc(nz, 0.0),
-      ca(nz), cc(nz), fa(nz + 1, 0.0), fc(nz + 1, 0.0), wlo(nz + 1, 0.0), whi(nz + 1, 0.0),
-      pdiag(nz);
+void metric_fill(int nz, double rdx2, double rdy2, const double* zf, double* out) {
+  const int L = nz + 1;
+  for (int i = 0; i < METRIC_ARRAYS * L; ++i) out[i] = 0.0;
+  double *dzc = out, *rdzc = out + L, *dzf = out + 2 * L, *rdzf = out + 3 * L, *pa = out + 4 * L,
+         *pc = out + 5 * L, *ca = out + 6 * L, *cc = out + 7 * L, *fa = out + 8 * L, *fc = out + 9 * L,
+         *wlo = out + 10 * L, *whi = out + 11 * L, *pdiag = out + 12 * L;
   for (int k = 0; k < nz; ++k) {
     dzc[k] = zf[k + 1] - zf[k];
     rdzc[k] = 1.0 / dzc[k];
@@ -38,13 +39,46 @@ void metric_host(int nz, double rdx2, double rdy2, const double* zf, std::vector
     wlo[k] = dzc[k - 1] / (2.0 * dzf[k]);
     whi[k] = dzc[k] / (2.0 * dzf[k]);
   }
-  const std::vector<double>* arrs[] = {&dzc, &rdzc, &dzf, &rdzf, &pa, &pc, &ca, &cc, &fa, &fc, &wlo, &whi, &pdiag};
-  flat.clear();
+}
+
+void metric_host(int nz, double rdx2, double rdy2, const double* zf, std::vector<double>& flat,
+                 std::vector<size_t>& offs) {
+  flat.assign((size_t)METRIC_ARRAYS * (nz + 1), 0.0);
+  metric_fill(nz, rdx2, rdy2, zf, flat.data());
   offs.clear();
-  for (auto* a : arrs) {
-    offs.push_back(flat.size());
-    flat.insert(flat.end(), a->begin(), a->end());
+  for (int a = 0; a < METRIC_ARRAYS; ++a) offs.push_back((size_t)a * (nz + 1));
+}
+
+// exp(-2 pi i m / N) with exact octant symmetry
+void twiddle(long long m, long long N, double& c, double& s) {
+  m %= N;
+  const long long q4 = N / 4, q8 = N / 8;
+  const long long quad = m / q4, r = m % q4;
+  double c0, s0;
+  if (r <= q8) {
+    const double a = 2.0 * M_PI * (double)r / (double)N;
+    c0 = std::cos(a);
+    s0 = std::sin(a);
+  } else {
+    const double a = 2.0 * M_PI * (double)(q4 - r) / (double)N;
+    c0 = std::sin(a);
+    s0 = std::cos(a);
   }
+  if (r == 0) { c0 = 1.0; s0 = 0.0; }
+  double cc, ss;
+  switch (quad) {
+    case 0: cc = c0; ss = s0; break;
+    case 1: cc = -s0; ss = c0; break;
+    case 2: cc = -c0; ss = -s0; break;
+    default: cc = s0; ss = -c0; break;
+  }
+  c = cc;
+  s = -ss;
+}
+
+double mod_wavenumber(int k, int n, double h) {
+  const double s = 2.0 * std::sin(M_PI * k / n) / h;
+  return s * s;
 }
 
 Metric metric_view(const double* mb, const std::vector<size_t>& offs) {
@@ -88,33 +122,6 @@ afid_status check_fields(std::initializer_list<const void*> ps) {
     if (!aligned(p)) return AFID_ERR_ALIGNMENT;
   }
   return AFID_OK;
-}
-
-// exp(-2 pi i m / N) with exact octant symmetry
-void twiddle(long long m, long long N, double& c, double& s) {
-  m %= N;
-  const long long q4 = N / 4, q8 = N / 8;
-  const long long quad = m / q4, r = m % q4;
-  double c0, s0;
-  if (r <= q8) {
-    const double a = 2.0 * M_PI * (double)r / (double)N;
-    c0 = std::cos(a);
-    s0 = std::sin(a);
-  } else {
-    const double a = 2.0 * M_PI * (double)(q4 - r) / (double)N;
-    c0 = std::sin(a);
-    s0 = std::cos(a);
-  }
-  if (r == 0) { c0 = 1.0; s0 = 0.0; }
-  double cc, ss;
-  switch (quad) {
-    case 0: cc = c0; ss = s0; break;
-    case 1: cc = -s0; ss = c0; break;
-    case 2: cc = -c0; ss = -s0; break;
-    default: cc = s0; ss = -c0; break;
-  }
-  c = cc;
-  s = -ss;
 }
 
 struct Alloc {
@@ -305,14 +312,8 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     twy32[m] = make_float2((float)twy[m].x, (float)twy[m].y);
   }
   std::vector<double> lamx(M + 1), lamy(g.nyh);
-  for (int k = 0; k <= M; ++k) {
-    const double s = 2.0 * std::sin(M_PI * k / nx) / g.dx;
-    lamx[k] = s * s;
-  }
-  for (int k = 0; k < g.nyh; ++k) {
-    const double s = 2.0 * std::sin(M_PI * k / ny) / g.dy;
-    lamy[k] = s * s;
-  }
+  for (int k = 0; k <= M; ++k) lamx[k] = mod_wavenumber(k, nx, g.dx);
+  for (int k = 0; k < g.nyh; ++k) lamy[k] = mod_wavenumber(k, ny, g.dy);
   std::vector<int> lowslot;
   std::vector<int2> low;
   if (mixed) {
@@ -588,6 +589,24 @@ afid_status afid_statistics(afid_ctx* c, const double* u, const double* v, const
     out->ke = sc[6];
   }
   return AFID_OK;
+}
+
+afid_status afid_nusselt(afid_ctx* c, const double* w, const double* T, double coef,
+                         double* nu_out, double* gw, double* gT) {
+  if (!c) return AFID_ERR_INVALID_ARG;
+  afid_status st = check_fields({w, T});
+  if (st) return st;
+  if (gw && !aligned(gw)) return AFID_ERR_ALIGNMENT;
+  if (gT && !aligned(gT)) return AFID_ERR_ALIGNMENT;
+  if (!std::isfinite(coef)) return AFID_ERR_INVALID_ARG;
+  if (nusselt(c, w, T, coef, gw, gT)) return AFID_ERR_CUDA;
+  if (nu_out) {
+    if (cudaMemcpyAsync(nu_out, c->stat_buf + (c->g.nz + 1), sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream))
+      return AFID_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream)) return AFID_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? AFID_OK : AFID_ERR_CUDA;
 }
 
 afid_status afid_poisson_solve_adjoint(afid_ctx* c, const double* gphi, double* grhs) {

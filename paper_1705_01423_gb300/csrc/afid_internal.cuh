@@ -160,16 +160,28 @@ struct afid_ctx {
   CUtensorMap tmy;
   int tma_y;
   int tmy_stages, tmy_threads, tmy_blocks_per_sm, tmy_tk;
+  int tma_stall_once;  // test of the timeout path: the next TMA launch stalls block 0
   size_t tmy_smem;
 };
 
 namespace afid {
 
-// Host wall-normal metric of the faces zf[0..nz] (the arrays of Metric, in its
-// order, concatenated in `flat`, offsets in `offs`), and the device view of
-// its uploaded copy.
+// Host wall-normal metric of the faces zf[0..nz]: the METRIC_ARRAYS arrays of
+// Metric, in its order, each nz+1 long (unused tail entries zero), written to
+// out[a (nz+1) + k] without any allocation (the allocation-free solve fills a
+// static staging buffer with it); metric_host returns the same in `flat` with
+// the offsets of the arrays in `offs`; metric_view is the device view of an
+// uploaded copy.
+constexpr int METRIC_ARRAYS = 13;
+void metric_fill(int nz, double rdx2, double rdy2, const double* zf, double* out);
 void metric_host(int nz, double rdx2, double rdy2, const double* zf, std::vector<double>& flat,
                  std::vector<size_t>& offs);
+// exp(-2 pi i m / N) as (c, s), evaluated in the first octant and mapped by
+// symmetry (the FFT twiddle tables)
+void twiddle(long long m, long long N, double& c, double& s);
+// modified wavenumber of the periodic 3-point second difference (Sec. 2.2):
+// 4 sin^2(pi k / n) / h^2
+double mod_wavenumber(int k, int n, double h);
 Metric metric_view(const double* dev, const std::vector<size_t>& offs);
 
 // launchers (stream-ordered; return cudaError_t of the launch)
@@ -202,6 +214,10 @@ cudaError_t statistics(afid_ctx* c, const double* u, const double* v, const doub
 cudaError_t statistics_grid(const Grid& g, const Metric& m, const afid_phys& ph, const double* u,
                             const double* v, const double* w, const double* T, double* stat_buf,
                             cudaStream_t st);
+// Volume Nusselt number 1 + coef <w T>_V into c->stat_buf[nz + 1] and, for
+// non-NULL gw / gT, its derivatives with respect to w and T.
+cudaError_t nusselt(afid_ctx* c, const double* w, const double* T, double coef, double* gw,
+                    double* gT);
 // b = D(u, v, w) / s (s from S_PROJ_S)
 cudaError_t divergence_to(afid_ctx* c, const double* u, const double* v, const double* w, double* b);
 // projection with s, beta read from S_PROJ_S / S_PROJ_BETA

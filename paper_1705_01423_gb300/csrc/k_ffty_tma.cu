@@ -16,8 +16,11 @@
 // A persistent block walks its tiles with a ring of S shared-memory stages:
 // while tile i is transformed, the load of tile i+1 and the store of tile i-1
 // are in flight (one mbarrier per stage for loads, bulk groups for stores).
-// Waits are bounded; a timeout sets the device flag S_FAULT and the block
-// stops after waiting (again bounded) for its own copies in flight.
+// Waits are bounded (2 s); a timeout sets the device flag S_FAULT and the block
+// stops after waiting (again bounded) for its own copies in flight. A test
+// hook (afid_test_tma_timeout) makes one launch's block 0 arm a stage without
+// issuing its copy, under a 1 ms limit, so that this path runs without any
+// fault or hang.
 #include "afid_internal.cuh"
 #include "fft.cuh"
 #include "tma.cuh"
@@ -41,7 +44,7 @@ __global__ void __launch_bounds__(kTmaMaxThreads, 1) k_fft_y_tma(const __grid_co
                                                        const typename cplx<R>::T* __restrict__ tw,
                                                        const double* __restrict__ skip,
                                                        double* __restrict__ scal, int stages,
-                                                       int ntile_x) {
+                                                       int ntile_x, int stall_block, uint64_t limit_ns) {
   using C = typename cplx<R>::T;
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -64,12 +67,16 @@ __global__ void __launch_bounds__(kTmaMaxThreads, 1) k_fft_y_tma(const __grid_co
   for (int q = tid; q < N; q += blockDim.x) stw[q] = tw[q];
   __syncthreads();
 
-  // thread 0: start the loads of local tile `it` into stage it % stages
+  // thread 0: start the loads of local tile `it` into stage it % stages. The
+  // block numbered stall_block (a test of the timeout path; -1 otherwise) arms
+  // its first stage with the tile's byte count and issues no copy, so that its
+  // wait runs out with nothing in flight for that stage.
   auto issue = [&](int it) {
     const int tile = first + it * gridDim.x;
     const int s = it % stages;
     const int kxt = tile % ntile_x, z = tile / ntile_x;
     mbar_expect_tx(&bar[s], tile_bytes);
+    if (it == 0 && (int)blockIdx.x == stall_block) return;
     for (int y0 = 0; y0 < N; y0 += BR)
       tma_load_3d(tiles + (size_t)s * tile_elems + (size_t)y0 * TK, &map, &bar[s], 2 * kxt * TK, y0, z);
   };
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(kTmaMaxThreads, 1) k_fft_y_tma(const __grid_co
       else bulk_wait_read<0>();
       issue(it + 1);
     }
-    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it / stages) & 1), kWaitLimitNs);
+    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((it / stages) & 1), limit_ns);
     if (__syncthreads_or(!ok)) {  // block-uniform decision
       failed = true;
       break;
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(kTmaMaxThreads, 1) k_fft_y_tma(const __grid_co
       scal[S_FAULT] = 1.0;
       // loads of tiles it and it+1 may still be in flight: wait for them (bounded)
       for (int q = it; q < count && q <= it + 1; ++q)
-        mbar_wait_bounded(&bar[q % stages], (uint32_t)((q / stages) & 1), kWaitLimitNs);
+        mbar_wait_bounded(&bar[q % stages], (uint32_t)((q / stages) & 1), limit_ns);
     }
     bulk_wait<0>();  // every store complete before the block's shared memory is released
   }
@@ -206,8 +213,13 @@ static void launch_tma(afid_ctx* c, const typename cplx<R>::T* tw, bool inv, con
   long long blocks = (long long)c->num_sms * c->tmy_blocks_per_sm;
   if (blocks > ntiles) blocks = ntiles;
   auto kf = inv ? k_fft_y_tma<R, true, TK> : k_fft_y_tma<R, false, TK>;
+  // a stall requested by afid_test_tma_timeout applies to one launch, with a
+  // 1 ms wait limit
+  const int stall = c->tma_stall_once ? 0 : -1;
+  const uint64_t limit = c->tma_stall_once ? 1000000ull : kWaitLimitNs;
+  c->tma_stall_once = 0;
   kf<<<(int)blocks, c->tmy_threads, c->tmy_smem, c->stream>>>(c->tmy, g, tw, skip, c->scal, c->tmy_stages,
-                                                               ntile_x);
+                                                               ntile_x, stall, limit);
 }
 
 template <typename R>
@@ -222,3 +234,10 @@ cudaError_t run_fft_y_tma(afid_ctx* c, const typename cplx<R>::T* tw, bool inv, 
 template cudaError_t run_fft_y_tma<float>(afid_ctx*, const float2*, bool, const double*);
 
 }  // namespace afid
+
+extern "C" afid_status afid_test_tma_timeout(afid_ctx* c) {
+  if (!c) return AFID_ERR_INVALID_ARG;
+  if (!c->tma_y) return AFID_ERR_INVALID_ARG;  // no TMA transform on this context
+  c->tma_stall_once = 1;
+  return AFID_OK;
+}

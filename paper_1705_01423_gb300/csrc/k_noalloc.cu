@@ -18,13 +18,11 @@ namespace {
 constexpr size_t kNoallocBytes = (size_t)16 << 20;  // 16 MiB per device
 __device__ __align__(256) unsigned char g_noalloc_ws[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
-void* g_ws_addr[kMaxDevices] = {};  // device address of g_noalloc_ws, per device
-std::mutex g_mu;                    // guards g_ws_addr and the host staging buffer
+std::mutex g_mu;  // serialises host callers: guards the host staging buffer
 
 // Host staging for the tables uploaded on every call (no heap allocation).
 constexpr int kMaxN = 4096;
-double g_stage[13 * (kMaxN + 1) + 2 * (2 * kMaxN) + 2 * (kMaxN / 2 + 1)];
+double g_stage[METRIC_ARRAYS * (kMaxN + 1) + 2 * (2 * kMaxN) + 2 * (kMaxN / 2 + 1)];
 
 size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -37,7 +35,7 @@ Layout layout(int nx, int ny, int nz) {
   Layout L;
   size_t o = 0;
   L.metric = o;
-  o += up256((size_t)13 * (nz + 1) * sizeof(double));
+  o += up256((size_t)METRIC_ARRAYS * (nz + 1) * sizeof(double));
   L.twx = o;
   o += up256((size_t)nx * sizeof(double2));
   L.twy = o;
@@ -58,35 +56,6 @@ Layout layout(int nx, int ny, int nz) {
 
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-void twiddle(long long m, long long N, double& c, double& s) {
-  m %= N;
-  const long long q4 = N / 4, q8 = N / 8;
-  const long long quad = m / q4, r = m % q4;
-  double c0, s0;
-  if (r <= q8) {
-    const double a = 2.0 * M_PI * (double)r / (double)N;
-    c0 = std::cos(a);
-    s0 = std::sin(a);
-  } else {
-    const double a = 2.0 * M_PI * (double)(q4 - r) / (double)N;
-    c0 = std::sin(a);
-    s0 = std::cos(a);
-  }
-  if (r == 0) {
-    c0 = 1.0;
-    s0 = 0.0;
-  }
-  double cc, ss;
-  switch (quad) {
-    case 0: cc = c0; ss = s0; break;
-    case 1: cc = -s0; ss = c0; break;
-    case 2: cc = -c0; ss = -s0; break;
-    default: cc = s0; ss = -c0; break;
-  }
-  c = cc;
-  s = -ss;
-}
-
 }  // namespace
 
 extern "C" afid_status afid_poisson_solve_noalloc(int nx, int ny, int nz, double lx, double ly,
@@ -105,16 +74,19 @@ extern "C" afid_status afid_poisson_solve_noalloc(int nx, int ny, int nz, double
 
   std::lock_guard<std::mutex> lock(g_mu);
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AFID_ERR_CUDA;
-  if (!g_ws_addr[dev]) {  // once per device, with that device current
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return AFID_ERR_CUDA;
-    }
-    g_ws_addr[dev] = p;
+  if (cudaGetDevice(&dev) != cudaSuccess) return AFID_ERR_CUDA;
+  // The array's device address, looked up on every call for the device and
+  // context current now (no allocation): an address cached from an earlier
+  // call could belong to another context of the same device, or to a context
+  // destroyed since by cudaDeviceReset, where the module is loaded again at
+  // another address. The first call on a device also loads the library's
+  // device code there.
+  void* wsp = nullptr;
+  if (cudaGetSymbolAddress(&wsp, g_noalloc_ws) != cudaSuccess || !wsp) {
+    cudaGetLastError();
+    return AFID_ERR_CUDA;
   }
-  unsigned char* ws = static_cast<unsigned char*>(g_ws_addr[dev]);
+  unsigned char* ws = static_cast<unsigned char*>(wsp);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   // ---- host tables, same formulas as afid_create
@@ -136,44 +108,14 @@ extern "C" afid_status afid_poisson_solve_noalloc(int nx, int ny, int nz, double
   g.rdy2 = g.rdy * g.rdy;
   const int Lz = nz + 1;
   double* h = g_stage;
-  double *dzc = h, *rdzc = h + Lz, *dzf = h + 2 * Lz, *rdzf = h + 3 * Lz, *pa = h + 4 * Lz,
-         *pc = h + 5 * Lz, *ca = h + 6 * Lz, *cc = h + 7 * Lz, *fa = h + 8 * Lz, *fc = h + 9 * Lz,
-         *wlo = h + 10 * Lz, *whi = h + 11 * Lz, *pdiag = h + 12 * Lz;
-  std::memset(h, 0, sizeof(double) * 13 * Lz);
-  for (int k = 0; k < nz; ++k) {
-    dzc[k] = zf[k + 1] - zf[k];
-    rdzc[k] = 1.0 / dzc[k];
-  }
-  dzf[0] = 0.5 * dzc[0];
-  dzf[nz] = 0.5 * dzc[nz - 1];
-  for (int k = 1; k < nz; ++k) dzf[k] = 0.5 * (zf[k] + zf[k + 1]) - 0.5 * (zf[k - 1] + zf[k]);
-  for (int k = 0; k <= nz; ++k) rdzf[k] = 1.0 / dzf[k];
-  for (int k = 0; k < nz; ++k) {
-    if (k > 0) pa[k] = 1.0 / (dzc[k] * dzf[k]);
-    if (k < nz - 1) pc[k] = 1.0 / (dzc[k] * dzf[k + 1]);
-    ca[k] = 1.0 / (dzc[k] * dzf[k]);
-    cc[k] = 1.0 / (dzc[k] * dzf[k + 1]);
-    pdiag[k] = pa[k] + pc[k] + 2.0 * g.rdx2 + 2.0 * g.rdy2;
-  }
-  for (int k = 1; k < nz; ++k) {
-    fa[k] = 1.0 / (dzf[k] * dzc[k - 1]);
-    fc[k] = 1.0 / (dzf[k] * dzc[k]);
-    wlo[k] = dzc[k - 1] / (2.0 * dzf[k]);
-    whi[k] = dzc[k] / (2.0 * dzf[k]);
-  }
-  double* tw = h + 13 * Lz;  // nx + ny complex
+  metric_fill(nz, g.rdx2, g.rdy2, zf, h);  // the arrays of Metric, each nz+1 long
+  double* tw = h + METRIC_ARRAYS * Lz;  // nx + ny complex
   for (int m = 0; m < nx; ++m) twiddle(m, nx, tw[2 * m], tw[2 * m + 1]);
   double* twy = tw + 2 * nx;
   for (int m = 0; m < ny; ++m) twiddle(m, ny, twy[2 * m], twy[2 * m + 1]);
   double* lam = twy + 2 * ny;  // M+1 then nyh
-  for (int k = 0; k <= M; ++k) {
-    const double s = 2.0 * std::sin(M_PI * k / nx) / g.dx;
-    lam[k] = s * s;
-  }
-  for (int k = 0; k < g.nyh; ++k) {
-    const double s = 2.0 * std::sin(M_PI * k / ny) / g.dy;
-    lam[M + 1 + k] = s * s;
-  }
+  for (int k = 0; k <= M; ++k) lam[k] = mod_wavenumber(k, nx, g.dx);
+  for (int k = 0; k < g.nyh; ++k) lam[M + 1 + k] = mod_wavenumber(k, ny, g.dy);
 
   // ---- device views into the fixed workspace
   const double* mb = reinterpret_cast<const double*>(ws + L.metric);
@@ -191,7 +133,7 @@ extern "C" afid_status afid_poisson_solve_noalloc(int nx, int ny, int nz, double
   c.device = dev;
 
   bool ok = true;
-  ok = ok && cudaMemcpyAsync(ws + L.metric, h, sizeof(double) * 13 * Lz, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(ws + L.metric, h, sizeof(double) * METRIC_ARRAYS * Lz, cudaMemcpyHostToDevice, st) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(ws + L.twx, tw, sizeof(double2) * nx, cudaMemcpyHostToDevice, st) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(ws + L.twy, twy, sizeof(double2) * ny, cudaMemcpyHostToDevice, st) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(ws + L.lamx, lam, sizeof(double) * (M + 1), cudaMemcpyHostToDevice, st) == cudaSuccess;

@@ -555,6 +555,64 @@ cudaError_t statistics(afid_ctx* c, const double* u, const double* v, const doub
   return statistics_grid(c->g, c->m, c->phys, u, v, w, T, c->stat_buf, c->stream);
 }
 
+// Volume Nusselt number (Sec. 5, Table 3; volume form Nu = 1 + coef <w T>_V
+// with coef = sqrt(Ra Pr) in free-fall units) and, when gw / gT are given, its
+// derivatives dNu/dw = f_k T and dNu/dT = f_k w with f_k = coef dx dy dzf_k / V
+// on the interior faces (zero on the walls) -- the cotangent seeds of the
+// adjoint rollout. One block per face plane k = 0..nz; the plane sum of w T
+// (interior planes) is formed in a fixed order and added by warp 0 into
+// psum[k] (deterministic), then k_nusselt_final adds dzf_k psum[k] over k.
+__global__ void __launch_bounds__(256) k_nusselt_planes(Grid g, Metric m, const double* __restrict__ w,
+                                                         const double* __restrict__ T, double fscale,
+                                                         double* __restrict__ gw, double* __restrict__ gT,
+                                                         double* __restrict__ psum) {
+  __shared__ double red[256];
+  const int k = blockIdx.x;
+  const size_t NXY = (size_t)g.nx * g.ny;
+  const size_t c0 = (size_t)k * NXY;
+  const bool interior = k > 0 && k < g.nz;
+  const double f = interior ? fscale * m.dzf[k] : 0.0;
+  double s = 0.0;
+  for (size_t c = threadIdx.x; c < NXY; c += blockDim.x) {
+    const double ww = w[c0 + c], t = T[c0 + c];
+    if (interior) s = fma(ww, t, s);
+    if (gw) gw[c0 + c] = f * t;
+    if (gT) gT[c0 + c] = f * ww;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) t += red[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) psum[k] = t;
+  }
+}
+
+// Nu = 1 + (coef dx dy / V) sum_k dzf_k psum[k] over the interior planes, one
+// lane, fixed order.
+__global__ void k_nusselt_final(Grid g, Metric m, const double* __restrict__ psum, double fscale,
+                                double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int k = 1; k < g.nz; ++k) s = fma(m.dzf[k], psum[k], s);
+  out[0] = 1.0 + fscale * s;
+}
+
+cudaError_t nusselt(afid_ctx* c, const double* w, const double* T, double coef, double* gw,
+                    double* gT) {
+  ProfScope ps(c, KF_ADJ);
+  const Grid& g = c->g;
+  double height = 0.0;
+  for (int k = 0; k < g.nz; ++k) height += c->zf_host[k + 1] - c->zf_host[k];
+  const double fscale = coef * g.dx * g.dy / (c->lx * c->ly * height);
+  double* psum = c->stat_buf;  // nz + 1 plane sums, then Nu
+  k_nusselt_planes<<<g.nz + 1, 256, 0, c->stream>>>(g, c->m, w, T, fscale, gw, gT, psum);
+  k_nusselt_final<<<1, 32, 0, c->stream>>>(g, c->m, psum, fscale, psum + (g.nz + 1));
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
 // Reduction of the per-block partials of the first mixed-precision forward
 // transform (k_r2c_x32<R32_FIRST>): weighted mean of b and ||b - mean||^2;
 // resets the refinement's scalars.

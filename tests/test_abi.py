@@ -118,3 +118,28 @@ def test_refined_grid_calls_reject_null_handles(L):
     assert L.afid_mr_scalar_advance(None, 1e-3, 1, None, None, None, None, None, None, None) == bad
     assert L.afid_mr_step(None, 1e-3, 1, None, None, None, None, None, None, None, None, None) == bad
     assert L.afid_mr_statistics(None, None, None, None, None, None, None) == bad
+
+
+def test_mixed_refinement_needs_at_least_one_iteration(L):
+    """refine_max_iter = 0 (and a negative or NaN tolerance) in AFID_MIXED is
+    refused on the host before any CUDA call; FP64 ignores both fields."""
+    from paper_1705_01423_gb300 import afid
+    z = np.ascontiguousarray(np.linspace(0.0, 1.0, 9))
+    h = C.c_void_p()
+    for it, tol in ((0, 1e-10), (-1, 1e-10), (4, -1.0), (4, float("nan"))):
+        d = afid.GridDesc(32, 16, 8, 1.0, 1.0, z.ctypes.data_as(C.POINTER(C.c_double)), afid.AFID_MIXED,
+                          tol, it, 0)
+        assert L.afid_create(C.byref(d), None, None, C.byref(h)) == afid.AFID_ERR_INVALID_ARG
+        assert not h.value
+        assert L.afid_workspace_bytes(C.byref(d)) == 0
+    d = afid.GridDesc(32, 16, 8, 1.0, 1.0, z.ctypes.data_as(C.POINTER(C.c_double)), afid.AFID_FP64, 1e-10, 0, 0)
+    assert L.afid_workspace_bytes(C.byref(d)) > 0
+
+
+def test_new_calls_reject_null_context(L):
+    from paper_1705_01423_gb300 import afid
+    bad = afid.AFID_ERR_INVALID_ARG
+    r = C.c_double()
+    assert L.afid_nusselt(None, None, None, 1.0, None, None, None) == bad
+    assert L.afid_probe_fp64_rate(None, 100, C.byref(r), None) == bad
+    assert L.afid_test_tma_timeout(None) == bad

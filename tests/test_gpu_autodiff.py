@@ -103,11 +103,20 @@ def rollout_dts(ctx, w, st, n):
 
 
 def nu_forward(ctx, st, dts, ra):
-    from paper_1705_01423_gb300.autodiff import _run_step, face_weights, nusselt
+    from paper_1705_01423_gb300.autodiff import _run_step
     S = [a.clone() for a in st]
     for dt in dts:
         _run_step(ctx, dt, S)
-    return nusselt(ctx, S[2], S[3], ra, 1.0, face_weights(ctx, S[0].device)), S
+    return ctx.nusselt(S[2], S[3], math.sqrt(ra)), S
+
+
+def face_weights(ctx, device):
+    """dx dy dzf_k on the interior faces, zero on the walls (test-side weights)."""
+    zf = torch.as_tensor(ctx._zf, dtype=torch.float64)
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    dzf = torch.zeros(ctx.nz + 1, dtype=torch.float64)
+    dzf[1:-1] = zc[1:] - zc[:-1]
+    return (ctx.lx / ctx.nx * ctx.ly / ctx.ny * dzf).to(device)
 
 
 def test_nusselt_gradient_vs_oracle_32cubed():
@@ -131,7 +140,6 @@ def fd_check(ctx, w, st, dts, ra, gT, ndir=4, eps=1e-6, seed=900):
     difference of the two Nusselt numbers summed face by face,
     sqrt(Ra Pr)/V sum_f W_f (w+ T+ - w- T-), so that the constant 1 and the
     large common part of <w T> do not cancel in floating point."""
-    from paper_1705_01423_gb300.autodiff import face_weights
     wf = face_weights(ctx, st[0].device)[:, None, None]
     coef = math.sqrt(ra) / (ctx.lx * ctx.ly)
     errs = []
@@ -176,3 +184,24 @@ def test_nusselt_gradient_fd_adjoint_workload():
     assert math.isfinite(nu) and float(gT.abs().max()) > 0
     errs = fd_check(ctx, w, st, dts, ra, gT)
     assert max(errs) < 1e-6, errs
+
+
+def test_afid_nusselt_and_seeds_vs_oracle():
+    """afid_nusselt against oracle.timestep.nusselt (1e-12) and its seed
+    cotangents against the oracle's reverse-mode derivative of Nu with respect
+    to w and T (1e-12 relative L2), on a stretched 48 x 40 x 21 grid."""
+    ra = 1e6
+    w = rb_workload(48, 40, 21, ra=ra)
+    g = ogrid(w)
+    st = initial(w, 3, amp=0.05, vel=0.1)
+    ctx = make_ctx(w)
+    W, T = gpu(st[2]), gpu(st[3])
+    nu, gw, gT = ctx.nusselt(W, T, math.sqrt(ra), seeds=True)
+    wr = cpu(st[2]).requires_grad_(True)
+    Tr = cpu(st[3]).requires_grad_(True)
+    nu_ref = ts.nusselt(g, wr, Tr, ra, 1.0)
+    nu_ref.backward()
+    assert abs(nu - float(nu_ref)) < 1e-12 * abs(float(nu_ref))
+    assert rel_l2(gw, wr.grad) < 1e-12 and rel_l2(gT, Tr.grad) < 1e-12
+    assert float(gw[0].abs().max()) == 0.0 and float(gT[-1].abs().max()) == 0.0
+    assert ctx.nusselt(W, T, math.sqrt(ra)) == nu       # deterministic, no seeds

@@ -14,7 +14,8 @@ import pytest
 import torch
 
 import synth
-from tests.helpers import gpu, make_ctx, rel_l2
+from oracle import poisson
+from tests.helpers import cpu, gpu, make_ctx, ogrid, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
@@ -35,7 +36,7 @@ def noalloc(w, rhs, phi):
     return st
 
 
-@pytest.mark.parametrize("shape", [(64, 64, 64), (32, 16, 13)])
+@pytest.mark.parametrize("shape", [(64, 64, 64), (32, 16, 13), (128, 128, 80)])
 def test_noalloc_matches_context_solve_twice(shape):
     nx, ny, nz = shape
     w = synth.workload("pc64", nx=nx, ny=ny, nz=nz, lx=1.7, ly=0.9)
@@ -47,6 +48,23 @@ def test_noalloc_matches_context_solve_twice(shape):
         assert noalloc(w, b, out) == 0
         torch.cuda.synchronize()
         assert rel_l2(out, ref) < TOL64
+
+
+def test_noalloc_in_place_and_against_the_oracle():
+    """rhs and phi may be the same buffer; the result is the FP64 solve of the
+    oracle within 1e-12 relative L2 (printed), on two calls in a row."""
+    nx, ny, nz = 32, 16, 13
+    w = synth.workload("pc64", nx=nx, ny=ny, nz=nz, lx=1.7, ly=0.9)
+    g = ogrid(w)
+    for seed in (201, 202):
+        b = synth.noise((nz, ny, nx), seed=seed) + 0.1
+        ref = poisson.solve(g, cpu(b))
+        x = gpu(b)
+        assert noalloc(w, x, x) == 0
+        torch.cuda.synchronize()
+        err = rel_l2(x, ref)
+        print("noalloc in place, seed %d: rel L2 vs oracle %.2e" % (seed, err))
+        assert err < TOL64
 
 
 def test_noalloc_rejects_oversized_grid():
