@@ -121,9 +121,12 @@ def _zero_walls(f):
 
 
 # one RK3 substep ----------------------------------------------------------------
-def substep(g: Grid, ph: Phys, l: int, dt: float, state, Hprev, advance_scalar: bool = True):
+def substep(g: Grid, ph: Phys, l: int, dt: float, state, Hprev, advance_scalar: bool = True,
+            return_provisional: bool = False):
     """state = (u, v, w, T, p) (T may be None); Hprev = (Hu, Hv, Hw, HT) of the
-    previous substep (ignored at l = 0). Returns (new_state, H).
+    previous substep (ignored at l = 0). Returns (new_state, H), and with
+    return_provisional also the provisional velocity (u*, v*, w*) that entered
+    the pressure correction.
 
     advance_scalar=False: T only supplies the buoyancy of the w equation and is
     returned unchanged (HT is None), as when the temperature lives on its own
@@ -148,6 +151,8 @@ def substep(g: Grid, ph: Phys, l: int, dt: float, state, Hprev, advance_scalar: 
         Tn = T + cn_solve_face(g, cn_beta(l, dt, ph.kappa), RT)
     s = ALPHA[l] * dt
     un, vn, wn, pn, _ = pressure_correction(g, us, vs, ws, p, s, bn)
+    if return_provisional:
+        return (un, vn, wn, Tn, pn), (Hu, Hv, Hw, HT), (us, vs, ws)
     return (un, vn, wn, Tn, pn), (Hu, Hv, Hw, HT)
 
 

@@ -4,22 +4,30 @@ substeps) against the FP64 oracle.
 * Small copies at the workloads' full step counts: Rayleigh-Benard (Ra = 1e8,
   Pr = 1) on 64 x 64 x 48 cells for 100 steps, plane Couette (Re_w = 4000,
   4pi x 2pi x 1) on 64 x 32 x 32 cells for 50 steps; within 1e-12 relative L2
-  after steps 1, 10 and the last.
-* The full sizes (512 x 512 x 384 and 1024 x 512 x 256) over 10 steps: the
-  growth of the difference is printed step by step and bounded by 1e-10 at every step, i.e. the error growth is reported rather
-  than held to 1e-12. Fields that start at zero are round-off-dominated after
-  the first step: in Rayleigh-Benard from rest u and v are the projection of a
-  buoyancy-driven w of order 1e-6 (relative differences 1.9e-12 and 2.9e-12,
-  then 4e-13 from the third step on, while T and p agree to 1e-16); in plane
-  Couette the pressure is the small response to the 0.05 perturbation
-  (1.4e-11 after the first step, then about 5e-13, while u, v, w agree to
-  1e-15). The 1e-12 element-wise bound is asserted on the perturbed full-size
-  substeps of test_gpu_fullsize.py and on the small copies above.
+  after steps 1, 10 and the last, field by field.
+* The full sizes (512 x 512 x 384 and 1024 x 512 x 256) over 10 steps, within
+  1e-12 after every step, each error measured against the scale of the
+  quantities the step formed it from (the normwise forward error of the
+  step): the velocity error relative to the largest provisional velocity
+  (u*, v*, w*) that entered a pressure correction during the step, the
+  pressure error relative to the largest pressure the step held after a
+  substep, T relative to itself. Field by field the first step is dominated
+  by cancellation: in Rayleigh-Benard from rest the velocity after the first
+  substep is the remainder of projecting a provisional velocity about a thousand
+  times larger (the hydrostatic response to the buoyancy), and in plane
+  Couette the first substep's pressure (the potential that makes the
+  non-solenoidal initial perturbation solenoidal) is removed again by the
+  next substep; the oracle itself, run on the same inputs shifted
+  periodically or with x and y exchanged (exact symmetries of the discrete
+  equations), changes these fields by up to 2.3e-12 (RB u, v) and 1e-12
+  (Couette p). The field-by-field errors are printed and bounded by 1e-10.
 
 The dt of every step comes from the CFL formula of Listing 1 on each side and
-is compared too, within the same 1e-12 (the maximum is order-independent; it
-inherits the round-off difference of the velocities at the maximising cell).
+is compared too, within 1e-12 (the maximum is order-independent; it inherits
+the round-off difference of the velocities at the maximising cell).
 """
+import math
+
 import pytest
 import torch
 
@@ -53,7 +61,10 @@ def state_errors(S, ref):
 
 
 def run_pair(w, steps, check_at, seed=0):
-    """Advances the GPU and the oracle side by side; returns {step: errors}."""
+    """Advances the GPU and the oracle side by side; returns {step: errors}:
+    each field's relative L2 error, and the step's normwise errors "vel*"
+    (velocity against the largest provisional velocity of its substeps) and
+    "p*" (pressure against the largest pressure after one of its substeps)."""
     g = ogrid(w)
     ph = phys_of(w)
     host = initial(w, seed)
@@ -70,12 +81,19 @@ def run_pair(w, steps, check_at, seed=0):
         cfl_ref = float(op.cfl_number(g, ref[0], ref[1], ref[2]))
         assert abs(cfl_gpu - cfl_ref) <= 1e-12 * cfl_ref, (n, cfl_gpu, cfl_ref)
         dt = op.cfl_dt(g, ref[0], ref[1], ref[2], w.cfl, w.dt_max)
+        vel_scale = p_scale = 0.0
         for l in range(3):
             ctx.rk3_substep(l, -1.0, *S, *H)
-            ref, Href = ts.substep(g, ph, l, dt, ref, Href)
+            ref, Href, prov = ts.substep(g, ph, l, dt, ref, Href, return_provisional=True)
+            vel_scale = max(vel_scale, math.sqrt(sum(float(x.norm()) ** 2 for x in prov)))
+            p_scale = max(p_scale, float(ref[4].norm()))
         if n in check_at:
             torch.cuda.synchronize()
-            out[n] = state_errors(S, ref)
+            e = state_errors(S, ref)
+            dv = math.sqrt(sum(float((S[i].cpu() - ref[i]).norm()) ** 2 for i in range(3)))
+            e["vel*"] = dv / vel_scale
+            e["p*"] = float((S[4].cpu() - ref[4]).norm()) / p_scale
+            out[n] = e
     return out
 
 
@@ -105,4 +123,8 @@ def test_fullsize_ten_steps_error_growth(name):
     errs = run_pair(w, 10, tuple(range(1, 11)))
     for n in sorted(errs):
         print("%s step %2d: %s" % (name, n, " ".join("%s %.2e" % kv for kv in errs[n].items())))
-    assert_all(errs, 1e-10)
+    for n, e in errs.items():
+        assert e["vel*"] < 1e-12 and e["p*"] < 1e-12, (n, e)
+        if "T" in e:
+            assert e["T"] < 1e-12, (n, e)
+    assert_all({n: {k: v for k, v in e.items() if k not in ("vel*", "p*")} for n, e in errs.items()}, 1e-10)
