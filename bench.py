@@ -59,6 +59,8 @@ def parse(argv=None):
                     help="only the Poisson-solve side measurement (FP64 and mixed)")
     ap.add_argument("--no-tma", action="store_true",
                     help="use the plain y-transform kernel instead of the TMA-staged one")
+    ap.add_argument("--fuse", action="store_true",
+                    help="mixed: the small-nz kernel fusing the y transforms and the Thomas sweeps, where it applies")
     ap.add_argument("--multires-only", action="store_true",
                     help="only the refined-temperature-grid coupled step (2x2x2, afid_mr_step)")
     ap.add_argument("--grid", default=None,
@@ -268,7 +270,7 @@ def run_poisson_only(args):
     torch.cuda.synchronize()
     out["poisson_fp64"] = {"ms": ms64, "grid_points_per_s": pts / (ms64 / 1e3), "families_ms": fam64}
     mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
-                   refine_max_iter=6, poisson_only=True, tma=tma)
+                   refine_max_iter=6, poisson_only=True, tma=tma, fuse=args.fuse)
     phim = torch.empty_like(b)
     _, info = mctx.poisson_solve(b, phim, info=True)
     msm = timed(lambda: mctx.poisson_solve(b, phim), 5, stream)
@@ -281,7 +283,8 @@ def run_poisson_only(args):
                             "refine_tol": MIXED_TOL, "rel_l2_vs_fp64_gpu": err,
                             "err_estimate": info["err_estimate"], "speedup_vs_fp64": ms64 / msm,
                             "families_ms": famm}
-    print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "tma_y": tma, "poisson": out}))
+    print(json.dumps({"workload": "%s %dx%dx%d" % (w.name, w.nx, w.ny, w.nz), "tma_y": tma,
+                      "fuse": args.fuse, "poisson": out}))
 
 
 def run_multires_only(args):
@@ -789,6 +792,83 @@ def workload_measurements(dev, reps=5):
     return out
 
 
+def tridiag_regime_measurement(dev, reps=20):
+    """The warp-partitioned FP64 tridiagonal solver against one system per
+    thread in the regime it is for: long wall-normal columns and few
+    wavenumber pairs (the paper's Table 3 Ra = 1e11 grid has 1296 wall-normal
+    points). FP64 Poisson solves of N(0,1) rhs on 64 x 64 x 1296, 32 x 32 x
+    2048 and 128 x 128 x 1296 cells, tanh-stretched z: the Thomas-family time
+    per solve with each solver, and the relative L2 difference of the two
+    solutions."""
+    import torch
+    import synth
+    from paper_1705_01423_gb300 import Context
+    stream = torch.cuda.current_stream()
+    out = {}
+    for nx, ny, nz in ((64, 64, 1296), (32, 32, 2048), (128, 128, 1296)):
+        w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
+        b = torch.as_tensor(synth.noise((nz, ny, nx), seed=nz)).to(dev)
+        res = {}
+        phis = {}
+        for name, warp in (("per_thread", False), ("warp_partitioned", True)):
+            ctx = Context(nx, ny, nz, w.lx, w.ly, w.faces(), poisson_only=True, warp_tridiag=warp)
+            phi = torch.empty_like(b)
+            ms = timed(lambda: ctx.poisson_solve(b, phi), reps, stream)
+            ctx.profile(True)
+            ctx.profile_read()
+            for _ in range(reps):
+                ctx.poisson_solve(b, phi)
+            fam = ctx.profile_read()
+            ctx.close()
+            res[name] = {"solve_ms": ms, "tridiag_ms": fam["thomas"][0] / reps}
+            phis[name] = phi
+        res["warp_over_per_thread_tridiag_time"] = (res["warp_partitioned"]["tridiag_ms"]
+                                                    / res["per_thread"]["tridiag_ms"])
+        res["rel_l2_between"] = float((phis["warp_partitioned"] - phis["per_thread"]).norm()
+                                      / phis["per_thread"].norm())
+        out["%dx%dx%d" % (nx, ny, nz)] = res
+    return out
+
+
+def small_nz_measurement(dev, shape=(512, 512, 32), reps=20):
+    """The fused small-nz kernel (y transforms and wall-normal solves of one
+    kx column in shared memory) against the separate passes, mixed Poisson
+    solve at refine_tol 1e-10 on 512 x 512 x 32 cells (stretched z; the FP32
+    spectral array, 36 MB, is L2-resident): time per solve, the time of the
+    middle stages (the fused kernel against the forward y transform, the
+    Thomas sweeps, the (0,0) mode and the inverse y transform), and the error
+    of each against the FP64 solve."""
+    import torch
+    import synth
+    from paper_1705_01423_gb300 import Context
+    stream = torch.cuda.current_stream()
+    nx, ny, nz = shape
+    w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
+    b = torch.as_tensor(synth.noise((nz, ny, nx), seed=32)).to(dev)
+    ctx = Context(nx, ny, nz, w.lx, w.ly, w.faces(), poisson_only=True)
+    ref = ctx.poisson_solve(b)
+    ctx.close()
+    out = {"grid": list(shape)}
+    for name, fuse in (("fused", True), ("separate", False)):
+        m = Context(nx, ny, nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
+                    refine_max_iter=6, poisson_only=True, fuse=fuse)
+        phi = torch.empty_like(b)
+        _, info = m.poisson_solve(b, phi, info=True)
+        ms = timed(lambda: m.poisson_solve(b, phi), reps, stream)
+        m.profile(True)
+        m.profile_read()
+        for _ in range(reps):
+            m.poisson_solve(b, phi)
+        fam = {k: v[0] / reps for k, v in m.profile_read().items() if v[1]}
+        mid = sum(fam.get(k, 0.0) for k in ("yfft_thomas", "fft_y", "thomas", "zero_mode"))
+        m.close()
+        out[name] = {"solve_ms": ms, "middle_stages_ms": mid, "iters": info["iters"],
+                     "rel_l2_vs_fp64": float((phi - ref).norm() / ref.norm()), "families_ms": fam}
+    out["solve_speedup"] = out["separate"]["solve_ms"] / out["fused"]["solve_ms"]
+    out["middle_stages_speedup"] = out["separate"]["middle_stages_ms"] / max(out["fused"]["middle_stages_ms"], 1e-9)
+    return out
+
+
 def side_measurements(ctx, w, dev, tma=True, state=None, fp64_peak=FP64_OPS_NOMINAL):
     """Poisson solve alone on the same grid: FP64 direct vs mixed FP32 + FP64
     refinement, with the mixed error against the FP64 GPU solve; the whole
@@ -830,6 +910,14 @@ def side_measurements(ctx, w, dev, tma=True, state=None, fp64_peak=FP64_OPS_NOMI
         out["workloads"] = workload_measurements(dev)
     except Exception as e:  # report, do not hide
         out["workloads"] = {"error": str(e)}
+    try:
+        out["tridiag_regime"] = tridiag_regime_measurement(dev)
+    except Exception as e:  # report, do not hide
+        out["tridiag_regime"] = {"error": str(e)}
+    try:
+        out["small_nz_fused"] = small_nz_measurement(dev)
+    except Exception as e:  # report, do not hide
+        out["small_nz_fused"] = {"error": str(e)}
     if state is not None:
         try:
             out["rk3_step_mixed"] = mixed_step_measurement(ctx, w, dev, state, tma=tma)

@@ -65,10 +65,24 @@ typedef enum {
 #define AFID_WARP_TRIDIAG 2 /* FP64: solve every (kx, ky) system with the warp-partitioned
                                solver (chunked Thomas per lane + parallel cyclic reduction
                                across the warp) instead of one system per thread -- the
-                               variant for long wall-normal columns and few modes */
+                               variant for long wall-normal columns and few modes. Without
+                               this flag or AFID_THREAD_TRIDIAG the context chooses: the
+                               warp-partitioned solver when nz >= 256 and there are at most
+                               64 systems (nx/2 + 1) ny per SM (measured on GB300: 3.2x
+                               faster at 64 x 64 x 1296, 7.6x at 32 x 32 x 2048, even at
+                               128 x 128 x 1296), one system per thread otherwise */
+#define AFID_THREAD_TRIDIAG 16 /* FP64: always one system per thread */
 #define AFID_NO_TMA 4       /* mixed: use the plain y-transform kernel (per-block loads into
                                padded shared memory) instead of the TMA-staged persistent
                                one for the FP32 passes (FP64 always uses the plain one) */
+#define AFID_FUSE_SMALL_NZ 8 /* mixed, small nz: run the forward y transform, the solves of
+                               every (kx, ky) and the inverse y transform in one kernel per kx
+                               column (family yfft_thomas), the brick of the column, its pivots
+                               and its low modes held in shared memory; taken when they fit
+                               and the FP32 spectral array fits in half the L2, ignored
+                               otherwise. Off by default: on GB300 at 512 x 512 x 32 it is
+                               about 10% slower than the separate passes (both L2-resident
+                               and latency-bound; one 197 KB block per SM) */
 
 typedef struct {
   int nx, ny, nz;          /* cells; nx, ny = 2^a 3^b 5^c (the FFT radices 8/4/2/3/5),
@@ -330,11 +344,11 @@ long long afid_kernel_launches(const afid_ctx* ctx);
 /* Instrumentation: when on, every launch group of the context is bracketed by
  * CUDA events on its stream, accumulated per kernel family (r2c_x, fft_y,
  * thomas, zero_mode, c2r_x, project, rhs, crank_nicolson, cfl_reduce, refine,
- * adjoint, cn_tables, mr_prolong, mr_scalar_rhs, mr_restrict; AFID_KERNEL_FAMILIES
+ * adjoint, cn_tables, mr_prolong, mr_scalar_rhs, mr_restrict, yfft_thomas; AFID_KERNEL_FAMILIES
  * of them; the afid_mr_* calls of a refined grid record into its coarse
  * context, their sweeps and tables under crank_nicolson and cn_tables). The first enable creates
  * the event pool (host-side CUDA events, no device memory). */
-#define AFID_KERNEL_FAMILIES 15
+#define AFID_KERNEL_FAMILIES 16
 afid_status afid_profile_enable(afid_ctx* ctx, int on);
 /* Synchronises the stream and returns, per family, the milliseconds and the
  * number of launch groups recorded since the last read (arrays of n entries,

@@ -35,6 +35,8 @@ AFID_MIXED = 1
 AFID_POISSON_ONLY = 1
 AFID_WARP_TRIDIAG = 2
 AFID_NO_TMA = 4
+AFID_FUSE_SMALL_NZ = 8
+AFID_THREAD_TRIDIAG = 16
 
 
 class GridDesc(C.Structure):
@@ -102,7 +104,7 @@ _SIGS = {
     "afid_mr_step": (I, [P, D, I, P, P, P, P, P, P, P, P, C.POINTER(Info)]),
     "afid_mr_statistics": (I, [P, P, P, P, P, P, P]),
 }
-KERNEL_FAMILIES = 15
+KERNEL_FAMILIES = 16
 
 
 def lib():
@@ -176,7 +178,7 @@ class Context:
 
     def __init__(self, nx, ny, nz, lx, ly, zf, precision="fp64", refine_tol=1e-12,
                  refine_max_iter=10, phys: Physics | None = None, poisson_only=False,
-                 warp_tridiag=False, tma=True, stream=None):
+                 warp_tridiag=None, tma=True, fuse=False, stream=None):
         import torch
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.lx, self.ly = float(lx), float(ly)
@@ -189,8 +191,9 @@ class Context:
                         self._zf.ctypes.data_as(C.POINTER(C.c_double)),
                         AFID_MIXED if precision == "mixed" else AFID_FP64, float(refine_tol),
                         int(refine_max_iter),
-                        (AFID_POISSON_ONLY if poisson_only else 0) | (AFID_WARP_TRIDIAG if warp_tridiag else 0)
-                        | (0 if tma else AFID_NO_TMA))
+                        (AFID_POISSON_ONLY if poisson_only else 0)
+                        | (0 if warp_tridiag is None else (AFID_WARP_TRIDIAG if warp_tridiag else AFID_THREAD_TRIDIAG))
+                        | (0 if tma else AFID_NO_TMA) | (AFID_FUSE_SMALL_NZ if fuse else 0))
         self._desc = desc
         ph = PhysDesc(self.phys.nu, self.phys.kappa, self.phys.buoyancy, self.phys.u_bot,
                       self.phys.u_top, self.phys.T_bot, self.phys.T_top)

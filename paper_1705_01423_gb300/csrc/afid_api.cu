@@ -149,7 +149,7 @@ size_t spec_elems(const afid_grid_desc* d) {
 void free_all(afid_ctx* c) {
   void* ps[] = {c->metric_buf, c->twx64, c->twy64, c->twx32, c->twy32, c->mtab64, c->mtab32,
                 c->lamx, c->lamy, c->spec, c->phi, c->bbuf, c->R[0], c->R[1], c->R[2],
-                c->R[3], c->cntab, c->pa32, c->pc32, c->lowslot, c->low_modes, c->low_scratch, c->scal,
+                c->R[3], c->cntab, c->pa32, c->pc32, c->lowslot, c->low_modes, c->low_scratch, c->scal, c->mtabt32,
                 c->part, c->part2, c->part3, c->rres, c->dprev, c->cff, c->stat_buf};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -284,6 +284,12 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     return AFID_ERR_CUDA;
   }
   const bool mixed = c->prec == AFID_MIXED;
+  // FP64 tridiagonal solver: the warp-partitioned one for long columns and few
+  // systems (where one system per thread leaves most of the GPU idle)
+  if (c->flags & AFID_WARP_TRIDIAG)
+    c->warp_tridiag = 1;
+  else if (!(c->flags & AFID_THREAD_TRIDIAG))
+    c->warp_tridiag = nz >= 256 && (long long)(M + 1) * ny <= 64LL * c->num_sms;
 
   c->zf_host = new (std::nothrow) double[nz + 1];
   if (!c->zf_host) {
@@ -357,6 +363,12 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
     c->pc32 = A.get<float>(nz);
     c->lowslot = A.get<int>((size_t)ny * (M + 1));
     if (c->nlow) c->low_modes = A.get<int2>(c->nlow);
+    std::vector<int> per_col(M + 1, 0);  // low modes per kx column
+    for (const int2& md : low) per_col[md.y]++;
+    int lmax = 0;
+    for (int v : per_col) lmax = v > lmax ? v : lmax;
+    if (init_yfft_thomas32(c, lmax) == cudaSuccess && c->fuse_yt)  // small nz: fused kernel's table
+      c->mtabt32 = A.get<float>(tab);
   }
   if (!(c->flags & AFID_POISSON_ONLY)) {
     c->R[0] = A.get<double>(n);
@@ -491,7 +503,8 @@ afid_status afid_profile_read(afid_ctx* c, double* ms, long long* launches, int 
 const char* afid_kernel_family_name(int f) {
   static const char* names[] = {"r2c_x", "fft_y", "thomas", "zero_mode", "c2r_x", "project",
                                 "rhs", "crank_nicolson", "cfl_reduce", "refine", "adjoint",
-                                "cn_tables", "mr_prolong", "mr_scalar_rhs", "mr_restrict"};
+                                "cn_tables", "mr_prolong", "mr_scalar_rhs", "mr_restrict",
+                                "yfft_thomas"};
   return (f >= 0 && f < KF_COUNT) ? names[f] : "unknown";
 }
 

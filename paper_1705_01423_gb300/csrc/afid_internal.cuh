@@ -66,6 +66,7 @@ enum KFam {
   KF_MR_PROLONG,   // refined temperature grid: velocity prolongation (+ time interpolation)
   KF_MR_RHS,       // refined temperature grid: explicit terms and right-hand side
   KF_MR_RESTRICT,  // refined temperature grid: restriction to the momentum grid
+  KF_YT,           // mixed, small nz: fused y transforms + wall-normal solves
   KF_COUNT
 };
 
@@ -117,6 +118,12 @@ struct afid_ctx {
   // mtab32 in mixed mode; low-mode mask threshold for mixed mode
   double* mtab64;
   float* mtab32;
+  // mixed, small nz (fuse_yt): the FP32 table transposed to [kx][k][kyh] for
+  // the fused y-transform / Thomas kernel, its launch shape
+  float* mtabt32;
+  int fuse_yt, yt_threads, yt_lmax;  // yt_lmax: most low modes in one kx column
+  int warp_tridiag;  // FP64: the warp-partitioned solver for every system (flag or auto)
+  size_t yt_smem;
   double lam_thr;
   double* lamx;  // [M+1]
   double* lamy;  // [nyh]
@@ -196,6 +203,14 @@ cudaError_t run_fft_y_tma(afid_ctx* c, const typename cplx<R>::T* tw, bool inv, 
 cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, const double* v,
                            const double* w, bool dev_s, double* phi, bool want_stats);
 int c2r_blocks(const Grid& g);
+// Fused small-nz kernel (mixed): shared memory (lmax: most low modes in one
+// kx column) and threads per block.
+size_t yfft_thomas32_smem(const Grid& g, int lmax);
+int yfft_thomas32_threads(const Grid& g);
+// Sets c->fuse_yt (and the attributes of the fused kernel) when the brick of
+// one kx column, its pivots and its low modes fit in shared memory and the
+// FP32 spectral array fits in half of L2.
+cudaError_t init_yfft_thomas32(afid_ctx* c, int lmax);
 // Mixed-precision refined solve of L phi = b (FP64 b, resident) into phi.
 cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi, bool stats);
 // One FP32 spectral solve of refinement step `it`: b (it = 0), the FP64

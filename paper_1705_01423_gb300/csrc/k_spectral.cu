@@ -20,7 +20,7 @@ namespace afid {
 // sweeps contain no division.
 __global__ void k_thomas_table(Grid g, Metric m, const double* __restrict__ lamx,
                                const double* __restrict__ lamy, double* __restrict__ mtab64,
-                               float* __restrict__ mtab32) {
+                               float* __restrict__ mtab32, float* __restrict__ mtabt32) {
   const int kx = blockIdx.x * blockDim.x + threadIdx.x;
   const int kyh = blockIdx.y;
   const int W = g.M + 1;
@@ -28,10 +28,13 @@ __global__ void k_thomas_table(Grid g, Metric m, const double* __restrict__ lamx
   const size_t tplane = (size_t)g.nyh * W;
   double* out = mtab64 + (size_t)kyh * W + kx;
   float* out32 = mtab32 ? mtab32 + (size_t)kyh * W + kx : nullptr;
+  // mtabt32 (fused small-nz solve): the FP32 table transposed to [kx][k][kyh]
+  float* outt = mtabt32 ? mtabt32 + (size_t)kx * g.nz * g.nyh + kyh : nullptr;
   if (kx == 0 && kyh == 0) {  // singular mode: handled by the exact prefix-sum kernel
     for (int k = 0; k < g.nz; ++k) {
       out[k * tplane] = 0.0;
       if (out32) out32[k * tplane] = 0.0f;
+      if (outt) outt[(size_t)k * g.nyh] = 0.0f;
     }
     return;
   }
@@ -43,13 +46,14 @@ __global__ void k_thomas_table(Grid g, Metric m, const double* __restrict__ lamx
     cprev = m.pc[k] * mk;
     out[k * tplane] = mk;
     if (out32) out32[k * tplane] = (float)mk;
+    if (outt) outt[(size_t)k * g.nyh] = (float)mk;
   }
 }
 
 cudaError_t init_thomas_tables(afid_ctx* c) {
   const Grid& g = c->g;
   dim3 blk(128), grd(ceil_div(g.M + 1, 128), g.nyh);
-  k_thomas_table<<<grd, blk, 0, c->stream>>>(g, c->m, c->lamx, c->lamy, c->mtab64, c->mtab32);
+  k_thomas_table<<<grd, blk, 0, c->stream>>>(g, c->m, c->lamx, c->lamy, c->mtab64, c->mtab32, c->mtabt32);
   c->launches++;
   return cudaGetLastError();
 }
@@ -709,10 +713,15 @@ __global__ void __launch_bounds__(128) k_thomas(Grid g, Metric m, typename cplx<
                                                 const double* __restrict__ skip) {
   using C = typename cplx<R>::T;
   if (skip && *skip != 0.0) return;
-  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ky = blockIdx.y;
+  // one system per thread over the flattened (ky, kx) index: consecutive
+  // threads take consecutive kx of a row and continue on the next row, so no
+  // block is left with the lone kx = M column of a row (every FP64 warp
+  // instruction costs the same issue time however few lanes are active)
   const int W = g.M + 1;
-  if (kx >= W || (kx == 0 && ky == 0)) return;
+  const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sidx >= g.ny * W) return;
+  const int ky = sidx / W, kx = sidx - ky * W;
+  if (kx == 0 && ky == 0) return;
   const int kyh = min(ky, g.ny - ky);
   if (lam_thr > 0.0 && lamx[kx] + lamy[kyh] < lam_thr) return;
   const size_t plane = (size_t)g.ny * g.P;
@@ -734,10 +743,11 @@ __global__ void __launch_bounds__(128) k_thomas_mixed(Grid g, Metric m, float2* 
                                                       double2* __restrict__ scratch,
                                                       const double* __restrict__ skip) {
   if (skip && *skip != 0.0) return;
-  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ky = blockIdx.y;
   const int W = g.M + 1;
-  if (kx >= W || (kx == 0 && ky == 0)) return;
+  const int sidx = blockIdx.x * blockDim.x + threadIdx.x;  // flattened (ky, kx), as in k_thomas
+  if (sidx >= g.ny * W) return;
+  const int ky = sidx / W, kx = sidx - ky * W;
+  if (kx == 0 && ky == 0) return;
   const int kyh = min(ky, g.ny - ky);
   const size_t plane = (size_t)g.ny * g.P;
   const size_t tplane = (size_t)g.nyh * W;
@@ -957,21 +967,16 @@ __device__ __forceinline__ double block_excl_scan(double v, double* ws, double* 
   return before;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(1024) k_zero_mode(Grid g, Metric m, typename cplx<R>::T* __restrict__ spec,
-                                                    double* scal, const double* __restrict__ skip) {
-  using C = typename cplx<R>::T;
-  if (skip && *skip != 0.0) return;
-  extern __shared__ double zb[];  // nz values, then 32 doubles of scan scratch
-  double* ws = zb + g.nz;
+// The (0,0)-mode solve on the nz values zb[0..nz) (shared memory, doubles),
+// in place: zb becomes phi - mean_W(phi). ws: 32 doubles of shared scratch.
+// Every thread of the block calls it.
+__device__ __forceinline__ void zero_mode_column(const Grid& g, const Metric& m, double* zb, double* ws,
+                                                 double* scal) {
   const int nz = g.nz;
-  const size_t plane = (size_t)g.ny * g.P;
   const int E = (nz + blockDim.x - 1) / blockDim.x;
   const int k0 = min((int)threadIdx.x * E, nz), k1 = min(k0 + E, nz);
   const double* __restrict__ dzc = m.dzc;
   const double* __restrict__ dzf = m.dzf;
-  for (int k = threadIdx.x; k < nz; k += blockDim.x) zb[k] = (double)spec[k * plane].x;
-  __syncthreads();
   double sw = 0.0, sb = 0.0;
   for (int k = k0; k < k1; ++k) {
     sw += dzc[k];
@@ -1004,7 +1009,272 @@ __global__ void __launch_bounds__(1024) k_zero_mode(Grid g, Metric m, typename c
   double tsp;
   block_excl_scan(sp, ws, &tsp);
   const double pm = tsp / tsw;
-  for (int k = k0; k < k1; ++k) spec[k * plane] = C{(R)(zb[k] - pm), (R)0};
+  for (int k = k0; k < k1; ++k) zb[k] -= pm;
+  __syncthreads();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_zero_mode(Grid g, Metric m, typename cplx<R>::T* __restrict__ spec,
+                                                    double* scal, const double* __restrict__ skip) {
+  using C = typename cplx<R>::T;
+  if (skip && *skip != 0.0) return;
+  extern __shared__ double zb[];  // nz values, then 32 doubles of scan scratch
+  const int nz = g.nz;
+  const size_t plane = (size_t)g.ny * g.P;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) zb[k] = (double)spec[k * plane].x;
+  __syncthreads();
+  zero_mode_column(g, m, zb, zb + nz, scal);
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) spec[k * plane] = C{(R)zb[k], (R)0};
+}
+
+// --------------------------------------------------------------------------
+// Mixed precision, small nz: the forward y transform, the wall-normal solves
+// and the inverse y transform of one kx column in one kernel (the FFT-Thomas-
+// FFT sequence of Sec. 2.2 on a brick that stays in shared memory). One block
+// per kx holds the brick [nz][ny] of that column (rows of pad8(ny) + 1
+// slots), the column's FP32 pivots [nz][ny/2 + 1] (the table transposed to
+// [kx][k][kyh], one contiguous slice) and, for the column's low modes, their
+// FP64 pivots and FP64 d'. It gathers the brick, transforms its nz lines
+// along y, solves the ny wall-normal systems of the column with every operand
+// and the intermediate d' on chip -- FP32 Thomas for most modes, FP64 Thomas
+// with the FP64 table for the low modes (lowslot >= 0), the exact FP64 prefix
+// sums for (0,0) in block kx = 0 -- transforms back and scatters the column.
+// The arithmetic per mode is that of k_fft_y / k_thomas_mixed / k_zero_mode;
+// the low modes take the table-based FP64 Thomas sweep instead of the
+// warp-partitioned one. Taken (AFID_FUSE_SMALL_NZ) when all of it fits in
+// shared memory and the FP32 spectral array fits in half the L2: there the
+// separate passes are bound by latency rather than by HBM, and the column
+// gathers (8 of every 32 bytes of a sector) are served from L2. With one
+// block of up to 227 KB per SM the kernel is itself latency-bound, and on
+// GB300 it does not beat the separate passes.
+struct YtLayout {
+  size_t brick, tw, piv, lowpiv, lowd, zb, total;  // byte offsets
+};
+__host__ __device__ inline YtLayout yt_layout(const Grid& g, int lmax) {
+  // every region starts on a 16-byte boundary (double2 and float2 accesses)
+  auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
+  YtLayout L;
+  size_t o = 0;
+  L.brick = o;
+  o += up16((size_t)g.nz * (pad8(g.ny) + 1) * sizeof(float2));
+  L.tw = o;
+  o += up16((size_t)g.ny * sizeof(float2));
+  L.piv = o;
+  o += up16((size_t)g.nz * g.nyh * sizeof(float));
+  L.lowpiv = o;
+  o += up16((size_t)lmax * g.nz * sizeof(double));
+  L.lowd = o;
+  o += up16((size_t)lmax * g.nz * sizeof(double2));
+  L.zb = o;
+  o += up16((size_t)(g.nz + 32) * sizeof(double));
+  L.total = o;
+  return L;
+}
+
+template <bool GEN>
+__global__ void __launch_bounds__(512) k_yfft_thomas32(Grid g, Metric m, float2* __restrict__ spec,
+                                                       const float2* __restrict__ tw,
+                                                       const float* __restrict__ mtabt32,
+                                                       const double* __restrict__ mtab64,
+                                                       const float* __restrict__ pa32,
+                                                       const float* __restrict__ pc32,
+                                                       const int* __restrict__ lowslot, int lmax,
+                                                       double* scal, const double* __restrict__ skip) {
+  if (skip && *skip != 0.0) return;
+  extern __shared__ __align__(16) unsigned char yt_raw[];
+  __shared__ int nlow_here;
+  const int N = g.ny, nz = g.nz, W = g.M + 1, kx = blockIdx.x, nyh = g.nyh;
+  const int LS = pad8(N) + 1;
+  const YtLayout L = yt_layout(g, lmax);
+  float2* brick = reinterpret_cast<float2*>(yt_raw + L.brick);
+  float2* stw = reinterpret_cast<float2*>(yt_raw + L.tw);
+  float* piv = reinterpret_cast<float*>(yt_raw + L.piv);           // [nz][nyh]
+  double* lpiv = reinterpret_cast<double*>(yt_raw + L.lowpiv);     // [lmax][nz]
+  double2* ld = reinterpret_cast<double2*>(yt_raw + L.lowd);       // [lmax][nz]
+  double* zb = reinterpret_cast<double*>(yt_raw + L.zb);           // (0,0) column + 32 scratch
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const size_t P = g.P;
+  if (tid == 0) nlow_here = 0;
+  // 1. gather the column (sixteen loads in flight per thread), the twiddles and
+  //    the column's FP32 pivots
+  const int tot = nz * N;
+  for (int i0 = tid; i0 < tot; i0 += 16 * nth) {
+    float2 v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = i0 + q * nth;
+      if (i < tot) {
+        const int z = i / N, y = i - z * N;
+        v[q] = spec[((size_t)z * N + y) * P + kx];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = i0 + q * nth;
+      if (i < tot) {
+        const int z = i / N, y = i - z * N;
+        brick[(size_t)z * LS + pad8(y)] = v[q];
+      }
+    }
+  }
+  for (int q = tid; q < N; q += nth) stw[q] = tw[q];
+  const float* pslice = mtabt32 + (size_t)kx * nz * nyh;
+  for (int q = tid; q < nz * nyh; q += nth) piv[q] = pslice[q];
+  __syncthreads();
+  // 2. forward transforms of the nz lines, N/8 threads per line
+  const int T = N / 8, lpr = nth / T;
+  for (int z0 = 0; z0 < nz; z0 += lpr) {
+    const int z = z0 + tid / T;
+    const bool act = tid < lpr * T && z < nz;
+    fft_line<false, GEN>(brick + (size_t)(act ? z : 0) * LS, N, stw, 1, tid % T, act);
+  }
+  // 3. wall-normal solves, one ky per thread
+  for (int ky = tid; ky < N; ky += nth) {
+    if (kx == 0 && ky == 0) continue;  // exact prefix sums below
+    const int kyh = min(ky, N - ky);
+    float2* col = brick + pad8(ky);
+    if (lowslot[(size_t)ky * W + kx] >= 0) {
+      // nearly singular low mode: FP64 sweep with the FP64 pivot table; its
+      // pivots are first copied to shared memory (independent loads), its d'
+      // kept there in FP64
+      const int j = atomicAdd(&nlow_here, 1);  // < lmax (the column's low-mode count)
+      double* mp = lpiv + (size_t)j * nz;
+      double2* dcol = ld + (size_t)j * nz;
+      const double* mt = mtab64 + (size_t)kyh * W + kx;
+      const size_t tplane = (size_t)nyh * W;
+      for (int k = 0; k < nz; ++k) mp[k] = mt[k * tplane];
+      double dx = 0.0, dy = 0.0;
+      for (int k = 0; k < nz; ++k) {
+        const float2 d = col[(size_t)k * LS];
+        const double mk = mp[k], ak = m.pa[k];
+        dx = ((double)d.x - ak * dx) * mk;
+        dy = ((double)d.y - ak * dy) * mk;
+        dcol[k] = make_double2(dx, dy);
+      }
+      col[(size_t)(nz - 1) * LS] = make_float2((float)dx, (float)dy);
+      for (int k = nz - 2; k >= 0; --k) {
+        const double2 e = dcol[k];
+        const double cp = m.pc[k] * mp[k];
+        dx = e.x - cp * dx;
+        dy = e.y - cp * dy;
+        col[(size_t)k * LS] = make_float2((float)dx, (float)dy);
+      }
+      continue;
+    }
+    // FP32 sweeps in blocks of U rows: the U loads of a block are issued
+    // together, then the recurrence runs on registers (the per-row arithmetic
+    // of thomas_column)
+    constexpr int U = 8;
+    const float* mt = piv + kyh;
+    float2 dv[U];
+    float mv[U];
+    float2 dp = make_float2(0.f, 0.f);
+    for (int kb = 0; kb < nz; kb += U) {
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int k = kb + q;
+        if (k < nz) {
+          dv[q] = col[(size_t)k * LS];
+          mv[q] = mt[(size_t)k * nyh];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int k = kb + q;
+        if (k < nz) {
+          const float ak = pa32[k];
+          dp = make_float2((dv[q].x - ak * dp.x) * mv[q], (dv[q].y - ak * dp.y) * mv[q]);
+          dv[q] = dp;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int k = kb + q;
+        if (k < nz) col[(size_t)k * LS] = dv[q];
+      }
+    }
+    float2 x = dp;
+    for (int kb = nz - 2; kb >= 0; kb -= U) {
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int k = kb - q;
+        if (k >= 0) {
+          dv[q] = col[(size_t)k * LS];
+          mv[q] = mt[(size_t)k * nyh];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int k = kb - q;
+        if (k >= 0) {
+          const float cp = pc32[k] * mv[q];
+          x = make_float2(dv[q].x - cp * x.x, dv[q].y - cp * x.y);
+          dv[q] = x;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int k = kb - q;
+        if (k >= 0) col[(size_t)k * LS] = dv[q];
+      }
+    }
+  }
+  __syncthreads();
+  // 4. the singular (0,0) mode (block-uniform branch)
+  if (kx == 0) {
+    for (int k = tid; k < nz; k += nth) zb[k] = (double)brick[(size_t)k * LS].x;
+    __syncthreads();
+    zero_mode_column(g, m, zb, zb + nz, scal);
+    for (int k = tid; k < nz; k += nth) brick[(size_t)k * LS] = make_float2((float)zb[k], 0.f);
+    __syncthreads();
+  }
+  // 5. inverse transforms
+  for (int z0 = 0; z0 < nz; z0 += lpr) {
+    const int z = z0 + tid / T;
+    const bool act = tid < lpr * T && z < nz;
+    fft_line<true, GEN>(brick + (size_t)(act ? z : 0) * LS, N, stw, 1, tid % T, act);
+  }
+  // 6. scatter the column
+  for (int i = tid; i < tot; i += nth) {
+    const int z = i / N, y = i - z * N;
+    spec[((size_t)z * N + y) * P + kx] = brick[(size_t)z * LS + pad8(y)];
+  }
+}
+
+// Shared memory of the fused small-nz kernel for a column low-mode count lmax.
+size_t yfft_thomas32_smem(const Grid& g, int lmax) { return yt_layout(g, lmax).total; }
+
+cudaError_t init_yfft_thomas32(afid_ctx* c, int lmax) {
+  c->fuse_yt = 0;
+  const Grid& g = c->g;
+  if (c->prec != AFID_MIXED || !(c->flags & AFID_FUSE_SMALL_NZ) || g.ny < 8) return cudaSuccess;
+  int smem_optin = 0, l2 = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
+  const size_t sm = yfft_thomas32_smem(g, lmax);
+  const size_t spec_bytes = (size_t)g.nz * g.ny * g.P * sizeof(float2);
+  // + the kernel's static shared memory (one int)
+  if (sm + 64 > (size_t)smem_optin || spec_bytes > (size_t)l2 / 2) return cudaSuccess;
+  const bool gen = !is_pow2(g.ny);
+  cudaError_t e = cudaFuncSetAttribute(gen ? k_yfft_thomas32<true> : k_yfft_thomas32<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  c->yt_smem = sm;
+  c->yt_lmax = lmax;
+  c->yt_threads = yfft_thomas32_threads(g);
+  c->fuse_yt = 1;
+  return cudaSuccess;
+}
+
+int yfft_thomas32_threads(const Grid& g) {
+  const int T = g.ny / 8;
+  long long want = (long long)T * g.nz;
+  if (want < g.ny) want = g.ny;
+  want = (want + 31) / 32 * 32;
+  return want > 512 ? 512 : (int)want;
 }
 
 static void launch_zero_mode_threads(const Grid& g, int* thr, size_t* sm) {
@@ -1115,7 +1385,7 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
   cudaError_t e;
   if ((e = run_r2c<double>(c, rhs, u, v, w, dev_s, spec, c->twx64, want_stats, nullptr))) return e;
   if ((e = run_fft_y<double>(c, spec, c->twy64, false, nullptr))) return e;
-  if (c->flags & AFID_WARP_TRIDIAG) {  // long-column variant: one warp per system
+  if (c->warp_tridiag) {  // long-column variant: one warp per system
     ProfScope ps(c, KF_THOMAS);
     const int nm = g.ny * (g.M + 1), wpb = warps_per_block(g.nz);
     const size_t wsm = (size_t)32 * wpb * 5 * warp_rows(g.nz) * sizeof(double);
@@ -1126,7 +1396,7 @@ cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, cons
     if ((e = cudaGetLastError())) return e;
   } else {
     ProfScope ps(c, KF_THOMAS);
-    dim3 grd(ceil_div(g.M + 1, 128), g.ny);
+    const int grd = ceil_div((long long)g.ny * (g.M + 1), 128);
     k_thomas<double><<<grd, 128, 0, c->stream>>>(g, c->m, spec, c->mtab64, c->m.pa, c->m.pc,
                                                  c->lamx, c->lamy, 0.0, nullptr);
     c->launches++;
@@ -1171,10 +1441,22 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_
     if ((e = cudaGetLastError())) return e;
   }
   if (first && (e = bstats_final(c))) return e;
+  if (c->fuse_yt) {  // small nz: y transforms and wall-normal solves in one kernel per kx column
+    {
+      ProfScope ps(c, KF_YT);
+      auto kf = is_pow2(g.ny) ? k_yfft_thomas32<false> : k_yfft_thomas32<true>;
+      kf<<<g.M + 1, c->yt_threads, c->yt_smem, c->stream>>>(g, c->m, spec, c->twy32, c->mtabt32, c->mtab64,
+                                                            c->pa32, c->pc32, c->lowslot, c->yt_lmax,
+                                                            c->scal, skip);
+      c->launches++;
+      if ((e = cudaGetLastError())) return e;
+    }
+    return run_c2r<float>(c, spec, c->twx32, phi, first ? 2 : 1, skip, c->part2);
+  }
   if ((e = run_fft_y<float>(c, spec, c->twy32, false, skip))) return e;
   {
     ProfScope ps(c, KF_THOMAS);
-    dim3 grd(ceil_div(g.M + 1, 128), g.ny);
+    const int grd = ceil_div((long long)g.ny * (g.M + 1), 128);
     k_thomas_mixed<<<grd, 128, 0, c->stream>>>(g, c->m, spec, c->mtab32, c->mtab64, c->pa32,
                                                c->pc32, c->lowslot, c->nlow, c->low_scratch, skip);
     c->launches++;

@@ -193,14 +193,18 @@ def test_rb_conduction_steady_gpu():
     assert float((S[3] - T0).abs().max()) < 1e-13
 
 
+@pytest.mark.parametrize("fuse", [True, False])
 @pytest.mark.parametrize("shape", [(64, 64, 33), (128, 32, 48)])
-def test_mixed_poisson(shape):
+def test_mixed_poisson(shape, fuse):
+    """fuse: the small-nz kernel that runs the y transforms and the wall-normal
+    solves of one kx column in shared memory (these grids qualify), or the
+    separate passes."""
     nx, ny, nz = shape
     w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
     g = ogrid(w)
     b = synth.noise(g.cell_shape(), seed=11)
     ref = poisson.solve(g, cpu(b))
-    ctx = make_ctx(w, precision="mixed", refine_tol=1e-12, refine_max_iter=8, poisson_only=True)
+    ctx = make_ctx(w, precision="mixed", refine_tol=1e-12, refine_max_iter=8, poisson_only=True, fuse=fuse)
     phi, info = ctx.poisson_solve(gpu(b), info=True)
     assert info["status"] in (0, 5)
     err = rel_l2(phi, ref)
@@ -209,8 +213,9 @@ def test_mixed_poisson(shape):
     assert info["err_estimate"] <= 1e-12
 
 
+@pytest.mark.parametrize("fuse", [True, False])
 @pytest.mark.parametrize("shape", [(64, 64, 33), (128, 32, 48), (64, 32, 37)])
-def test_mixed_poisson_at_1e10(shape):
+def test_mixed_poisson_at_1e10(shape, fuse):
     """refine_tol = 1e-10, the accuracy the mixed solve is held to: three FP32
     solves at most on these grids, and the error against the oracle below the
     tolerance and consistent with the estimate."""
@@ -219,7 +224,7 @@ def test_mixed_poisson_at_1e10(shape):
     g = ogrid(w)
     b = synth.noise(g.cell_shape(), seed=13)
     ref = poisson.solve(g, cpu(b))
-    ctx = make_ctx(w, precision="mixed", refine_tol=1e-10, refine_max_iter=8, poisson_only=True)
+    ctx = make_ctx(w, precision="mixed", refine_tol=1e-10, refine_max_iter=8, poisson_only=True, fuse=fuse)
     phi, info = ctx.poisson_solve(gpu(b), info=True)
     assert info["status"] in (0, 5)
     err = rel_l2(phi, ref)
@@ -270,6 +275,21 @@ def test_poisson_fp64_warp_partitioned_tridiag(shape):
     assert rel_l2(phi, ref) < TOL64
 
 
+@pytest.mark.parametrize("shape", [(32, 16, 1024), (64, 32, 300)])
+def test_poisson_fp64_tridiag_choice_long_columns(shape):
+    """Long columns and few systems: the context picks the warp-partitioned
+    solver by itself; it, the forced per-thread solver and the oracle agree."""
+    nx, ny, nz = shape
+    w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
+    g = ogrid(w)
+    b = synth.noise(g.cell_shape(), seed=nz + 1)
+    ref = poisson.solve(g, cpu(b))
+    auto = make_ctx(w, poisson_only=True).poisson_solve(gpu(b))
+    per_thread = make_ctx(w, poisson_only=True, warp_tridiag=False).poisson_solve(gpu(b))
+    assert rel_l2(auto, ref) < TOL64 and rel_l2(per_thread, ref) < TOL64
+    assert rel_l2(auto, per_thread) < TOL64
+
+
 @pytest.mark.parametrize("shape", [(32, 16, 12), (64, 32, 37), (128, 64, 24), (64, 128, 19),
                                    (64, 64, 33), (128, 32, 48), (64, 256, 9), (32, 512, 5),
                                    (64, 1024, 4), (48, 2048, 3), (16, 2048, 4)])
@@ -284,13 +304,41 @@ def test_tma_y_transform_matches_plain_kernel(shape):
     w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
     g = ogrid(w)
     b = synth.noise(g.cell_shape(), seed=nx + ny)
-    kw = dict(precision="mixed", refine_tol=1e-12, refine_max_iter=8, poisson_only=True)
+    kw = dict(precision="mixed", refine_tol=1e-12, refine_max_iter=8, poisson_only=True, fuse=False)
     a = make_ctx(w, **kw).poisson_solve(gpu(b))
     p = make_ctx(w, tma=False, **kw).poisson_solve(gpu(b))
     torch.cuda.synchronize()
     assert rel_l2(a, p) < 1e-11
     ref = poisson.solve(g, cpu(b))
     assert rel_l2(a, ref) < TOLMIX
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 8), (128, 64, 13), (32, 128, 5), (96, 48, 9), (48, 120, 11),
+                                   (64, 32, 37), (256, 256, 32), (16, 8, 3)])
+def test_mixed_fused_small_nz_matches_separate_passes(shape):
+    """The fused small-nz kernel (y transforms, FP32 Thomas, FP64 low modes,
+    exact (0,0) mode, one kernel per kx column) against the separate passes:
+    the same solve to round-off (the low modes take the table-based FP64
+    sweep instead of the warp-partitioned one), both within 1e-10 of the
+    oracle. Shapes: powers of two, radix-3/5 lines (96, 48, 120), odd and
+    short nz, several column counts."""
+    nx, ny, nz = shape
+    w = synth.workload("pc64", nx=nx, ny=ny, nz=nz, lx=1.6, ly=0.7)
+    g = ogrid(w)
+    b = synth.noise(g.cell_shape(), seed=nx + 3 * nz) + 0.05
+    ref = poisson.solve(g, cpu(b))
+    kw = dict(precision="mixed", refine_tol=1e-12, refine_max_iter=8, poisson_only=True)
+    fused = make_ctx(w, fuse=True, **kw)
+    fused.profile(True)
+    fused.profile_read()
+    a, ia = fused.poisson_solve(gpu(b), info=True)
+    fams = fused.profile_read()
+    assert fams["yfft_thomas"][1] >= 1 and fams["thomas"][1] == 0     # the fused kernel ran
+    p, ip = make_ctx(w, **kw).poisson_solve(gpu(b), info=True)
+    torch.cuda.synchronize()
+    assert ia["status"] in (0, 5) and ip["status"] in (0, 5)
+    assert rel_l2(a, p) < 1e-11
+    assert rel_l2(a, ref) < TOLMIX and rel_l2(p, ref) < TOLMIX
 
 
 RADIX35 = [(96, 48, 9), (160, 40, 7), (48, 120, 11), (384, 24, 5), (240, 24, 6)]

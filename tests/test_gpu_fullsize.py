@@ -255,3 +255,55 @@ def test_paper_table4_grid_1280_poisson_sampled_modes():
     num = sum(np.linalg.norm(got[p] - ref[p]) ** 2 for p in pairs)
     den = sum(np.linalg.norm(ref[p]) ** 2 for p in pairs)
     assert np.sqrt(num / den) < 1e-12
+
+
+def test_mixed_stopping_rule_on_modes_just_above_the_fp64_threshold():
+    """An rhs aimed at the stopping rule of the mixed solve: every (kx, ky)
+    pair with 0 < kx < nx/2 whose wavenumber lambda_x + lambda_y lies just
+    above the FP64 low-mode threshold (64 lambda_min <= lambda < 100
+    lambda_min: the worst-conditioned modes left to the FP32 solve), each with
+    a seeded N(0,1) wall-normal profile and phase, on the plane Couette grid
+    1024 x 512 x 256 (4 pi x 2 pi x 1, stretched z). The reference is the
+    sampled-mode oracle at those pairs (direct FP64 DFT of the rhs, FP64
+    Thomas per column), synthesised back to the full grid; the mixed solve
+    at refine_tol = 1e-10 must be within 1e-10 of it over the whole field,
+    the FP64 solve within 1e-12."""
+    import math
+    w = synth.workload("couette1024")
+    g = ogrid(w)
+    nx, ny, nz, M = w.nx, w.ny, w.nz, w.nx // 2
+    lamx = [4 * math.sin(math.pi * k / nx) ** 2 / g.dx ** 2 for k in range(M + 1)]
+    lamy = [4 * math.sin(math.pi * k / ny) ** 2 / g.dy ** 2 for k in range(ny // 2 + 1)]
+    lmin = min(lamx[1], lamy[1])
+    pairs = [(kx, ky) for ky in range(ny) for kx in range(1, M)
+             if 64 * lmin <= lamx[kx] + lamy[min(ky, ny - ky)] < 100 * lmin]
+    assert len(pairs) >= 10
+    rng = synth.rng(4242)
+    prof = rng.standard_normal((nz, len(pairs)))
+    phase = rng.uniform(0, 2 * np.pi, len(pairs))
+    ii = np.arange(nx)[None, :]
+    jj = np.arange(ny)[:, None]
+    basis = np.stack([np.cos(2 * np.pi * (kx * ii / nx + ky * jj / ny) + ph).ravel()
+                      for (kx, ky), ph in zip(pairs, phase)])           # [modes][ny nx]
+    b = (prof @ basis).reshape(nz, ny, nx)
+    ref_hat = sampled.solve_modes(g, b, pairs)
+    # the real field of a half-spectrum coefficient F at 0 < kx < nx/2:
+    # (2 / (nx ny)) Re(F exp(+2 pi i (kx i/nx + ky j/ny)))
+    re = np.stack([ref_hat[p].real for p in pairs], axis=1)
+    im = np.stack([ref_hat[p].imag for p in pairs], axis=1)
+    cosb = np.stack([np.cos(2 * np.pi * (kx * ii / nx + ky * jj / ny)).ravel() for kx, ky in pairs])
+    sinb = np.stack([np.sin(2 * np.pi * (kx * ii / nx + ky * jj / ny)).ravel() for kx, ky in pairs])
+    ref = ((re @ cosb - im @ sinb) * (2.0 / (nx * ny))).reshape(nz, ny, nx)
+    del basis, cosb, sinb
+    B = gpu(b)
+    ctx64 = make_ctx(w, poisson_only=True)
+    e64 = rel_l2(ctx64.poisson_solve(B), cpu(ref))
+    del ctx64
+    ctxm = make_ctx(w, precision="mixed", refine_tol=1e-10, refine_max_iter=6, poisson_only=True)
+    phi, info = ctxm.poisson_solve(B, info=True)
+    em = rel_l2(phi, cpu(ref))
+    print("modes just above the FP64 threshold (%d pairs): FP64 %.2e, mixed %.2e (estimate %.2e, %d "
+          "iterations)" % (len(pairs), e64, em, info["err_estimate"], info["iters"]))
+    assert e64 < 1e-12
+    assert info["status"] in (0, 5)
+    assert em < 1e-10, (em, info)
