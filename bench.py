@@ -59,8 +59,9 @@ def parse(argv=None):
                     help="only the Poisson-solve side measurement (FP64 and mixed)")
     ap.add_argument("--no-tma", action="store_true",
                     help="use the plain y-transform kernel instead of the TMA-staged one")
-    ap.add_argument("--fuse", action="store_true",
-                    help="mixed: the small-nz kernel fusing the y transforms and the Thomas sweeps, where it applies")
+    ap.add_argument("--fuse", default="auto", choices=["auto", "on", "off"],
+                    help="mixed: the small-nz kernel fusing the y transforms and the Thomas sweeps "
+                         "(auto: where measured faster; on: wherever it fits; off: never)")
     ap.add_argument("--multires-only", action="store_true",
                     help="only the refined-temperature-grid coupled step (2x2x2, afid_mr_step)")
     ap.add_argument("--grid", default=None,
@@ -270,7 +271,8 @@ def run_poisson_only(args):
     torch.cuda.synchronize()
     out["poisson_fp64"] = {"ms": ms64, "grid_points_per_s": pts / (ms64 / 1e3), "families_ms": fam64}
     mctx = Context(w.nx, w.ny, w.nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
-                   refine_max_iter=6, poisson_only=True, tma=tma, fuse=args.fuse)
+                   refine_max_iter=6, poisson_only=True, tma=tma,
+                   fuse={"auto": None, "on": True, "off": False}[args.fuse])
     phim = torch.empty_like(b)
     _, info = mctx.poisson_solve(b, phim, info=True)
     msm = timed(lambda: mctx.poisson_solve(b, phim), 5, stream)
@@ -503,9 +505,20 @@ def run_ours(args):
             e3.record(stream)
             torch.cuda.synchronize()
             times[name] = max_over_ranks(e2.elapsed_time(e3), world, dev)
+        # the host link alone: one state upload and one read-back, each by itself
+        link = {}
+        for name, fn in (("h2d", lambda: copy_all(S, hS)), ("d2h", lambda: copy_all(oS, S))):
+            e2 = torch.cuda.Event(enable_timing=True)
+            e3 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e2.record(stream)
+            fn()
+            e3.record(stream)
+            torch.cuda.synchronize()
+            link[name + "_gbs"] = bi / (e2.elapsed_time(e3) / 1e3) / 1e9
         e2e = {"value": whole_job_rate(pts, world, k2, times["pipelined"]), "unit": "grid-points/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "steps": k2,
-               "serial_value": whole_job_rate(pts, world, k2, times["serial"]),
+               "serial_value": whole_job_rate(pts, world, k2, times["serial"]), "host_link": link,
                "note": "every step uploads its state from pinned host memory and reads its result back; "
                        "value: uploads and read-backs on two copy streams overlapping the neighbouring "
                        "steps (two device state buffers); serial_value: copy, step, copy in order"}
@@ -830,43 +843,49 @@ def tridiag_regime_measurement(dev, reps=20):
     return out
 
 
-def small_nz_measurement(dev, shape=(512, 512, 32), reps=20):
+def small_nz_measurement(dev, shapes=((512, 512, 8), (256, 256, 16), (512, 512, 32)), reps=20):
     """The fused small-nz kernel (y transforms and wall-normal solves of one
     kx column in shared memory) against the separate passes, mixed Poisson
-    solve at refine_tol 1e-10 on 512 x 512 x 32 cells (stretched z; the FP32
-    spectral array, 36 MB, is L2-resident): time per solve, the time of the
-    middle stages (the fused kernel against the forward y transform, the
-    Thomas sweeps, the (0,0) mode and the inverse y transform), and the error
-    of each against the FP64 solve."""
+    solve at refine_tol 1e-10 on small-nz grids (stretched z; the FP32
+    spectral arrays are L2-resident): time per solve, the time of the middle
+    stages (the fused kernel against the forward y transform, the Thomas
+    sweeps, the (0,0) mode and the inverse y transform), the error of each
+    against the FP64 solve, and which form the context chooses by itself."""
     import torch
     import synth
     from paper_1705_01423_gb300 import Context
     stream = torch.cuda.current_stream()
-    nx, ny, nz = shape
-    w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
-    b = torch.as_tensor(synth.noise((nz, ny, nx), seed=32)).to(dev)
-    ctx = Context(nx, ny, nz, w.lx, w.ly, w.faces(), poisson_only=True)
-    ref = ctx.poisson_solve(b)
-    ctx.close()
-    out = {"grid": list(shape)}
-    for name, fuse in (("fused", True), ("separate", False)):
-        m = Context(nx, ny, nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
-                    refine_max_iter=6, poisson_only=True, fuse=fuse)
-        phi = torch.empty_like(b)
-        _, info = m.poisson_solve(b, phi, info=True)
-        ms = timed(lambda: m.poisson_solve(b, phi), reps, stream)
-        m.profile(True)
-        m.profile_read()
-        for _ in range(reps):
-            m.poisson_solve(b, phi)
-        fam = {k: v[0] / reps for k, v in m.profile_read().items() if v[1]}
-        mid = sum(fam.get(k, 0.0) for k in ("yfft_thomas", "fft_y", "thomas", "zero_mode"))
-        m.close()
-        out[name] = {"solve_ms": ms, "middle_stages_ms": mid, "iters": info["iters"],
-                     "rel_l2_vs_fp64": float((phi - ref).norm() / ref.norm()), "families_ms": fam}
-    out["solve_speedup"] = out["separate"]["solve_ms"] / out["fused"]["solve_ms"]
-    out["middle_stages_speedup"] = out["separate"]["middle_stages_ms"] / max(out["fused"]["middle_stages_ms"], 1e-9)
-    return out
+    res = {}
+    for shape in shapes:
+        nx, ny, nz = shape
+        w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
+        b = torch.as_tensor(synth.noise((nz, ny, nx), seed=32)).to(dev)
+        ctx = Context(nx, ny, nz, w.lx, w.ly, w.faces(), poisson_only=True)
+        ref = ctx.poisson_solve(b)
+        ctx.close()
+        out = {}
+        for name, fuse in (("fused", True), ("separate", False), ("default", None)):
+            m = Context(nx, ny, nz, w.lx, w.ly, w.faces(), precision="mixed", refine_tol=MIXED_TOL,
+                        refine_max_iter=6, poisson_only=True, fuse=fuse)
+            phi = torch.empty_like(b)
+            _, info = m.poisson_solve(b, phi, info=True)
+            ms = timed(lambda: m.poisson_solve(b, phi), reps, stream)
+            m.profile(True)
+            m.profile_read()
+            for _ in range(reps):
+                m.poisson_solve(b, phi)
+            fam = {k: v[0] / reps for k, v in m.profile_read().items() if v[1]}
+            mid = sum(fam.get(k, 0.0) for k in ("yfft_thomas", "fft_y", "thomas", "zero_mode"))
+            m.close()
+            out[name] = {"solve_ms": ms, "middle_stages_ms": mid, "iters": info["iters"],
+                         "rel_l2_vs_fp64": float((phi - ref).norm() / ref.norm()),
+                         "fused": "yfft_thomas" in fam}
+        out["solve_speedup"] = out["separate"]["solve_ms"] / out["fused"]["solve_ms"]
+        out["middle_stages_speedup"] = (out["separate"]["middle_stages_ms"]
+                                        / max(out["fused"]["middle_stages_ms"], 1e-9))
+        out["default_is_fused"] = out["default"]["fused"]
+        res["%dx%dx%d" % shape] = out
+    return res
 
 
 def side_measurements(ctx, w, dev, tma=True, state=None, fp64_peak=FP64_OPS_NOMINAL):

@@ -78,11 +78,14 @@ typedef enum {
 #define AFID_FUSE_SMALL_NZ 8 /* mixed, small nz: run the forward y transform, the solves of
                                every (kx, ky) and the inverse y transform in one kernel per kx
                                column (family yfft_thomas), the brick of the column, its pivots
-                               and its low modes held in shared memory; taken when they fit
-                               and the FP32 spectral array fits in half the L2, ignored
-                               otherwise. Off by default: on GB300 at 512 x 512 x 32 it is
-                               about 10% slower than the separate passes (both L2-resident
-                               and latency-bound; one 197 KB block per SM) */
+                               and its low modes held in shared memory, wherever they fit and
+                               the FP32 spectral array fits in half the L2. Without this flag
+                               or AFID_NO_FUSE the context fuses where it was measured faster
+                               on GB300: nz ny <= 8192 and ny <= 512 (the three stages 1.4-2.1x
+                               faster, e.g. 0.13 against 0.28 ms at 512 x 512 x 8); at larger
+                               bricks (512 x 512 x 32, 1024 x 1024 x 8) the fused kernel, one
+                               block per SM, is 10% slower than the separate passes */
+#define AFID_NO_FUSE 32     /* mixed: never fuse (the separate y-transform and Thomas passes) */
 
 typedef struct {
   int nx, ny, nz;          /* cells; nx, ny = 2^a 3^b 5^c (the FFT radices 8/4/2/3/5),

@@ -36,6 +36,7 @@ AFID_POISSON_ONLY = 1
 AFID_WARP_TRIDIAG = 2
 AFID_NO_TMA = 4
 AFID_FUSE_SMALL_NZ = 8
+AFID_NO_FUSE = 32
 AFID_THREAD_TRIDIAG = 16
 
 
@@ -178,7 +179,7 @@ class Context:
 
     def __init__(self, nx, ny, nz, lx, ly, zf, precision="fp64", refine_tol=1e-12,
                  refine_max_iter=10, phys: Physics | None = None, poisson_only=False,
-                 warp_tridiag=None, tma=True, fuse=False, stream=None):
+                 warp_tridiag=None, tma=True, fuse=None, stream=None):
         import torch
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.lx, self.ly = float(lx), float(ly)
@@ -193,7 +194,7 @@ class Context:
                         int(refine_max_iter),
                         (AFID_POISSON_ONLY if poisson_only else 0)
                         | (0 if warp_tridiag is None else (AFID_WARP_TRIDIAG if warp_tridiag else AFID_THREAD_TRIDIAG))
-                        | (0 if tma else AFID_NO_TMA) | (AFID_FUSE_SMALL_NZ if fuse else 0))
+                        | (0 if tma else AFID_NO_TMA) | (0 if fuse is None else (AFID_FUSE_SMALL_NZ if fuse else AFID_NO_FUSE)))
         self._desc = desc
         ph = PhysDesc(self.phys.nu, self.phys.kappa, self.phys.buoyancy, self.phys.u_bot,
                       self.phys.u_top, self.phys.T_bot, self.phys.T_top)

@@ -1041,12 +1041,13 @@ __global__ void __launch_bounds__(1024) k_zero_mode(Grid g, Metric m, typename c
 // sums for (0,0) in block kx = 0 -- transforms back and scatters the column.
 // The arithmetic per mode is that of k_fft_y / k_thomas_mixed / k_zero_mode;
 // the low modes take the table-based FP64 Thomas sweep instead of the
-// warp-partitioned one. Taken (AFID_FUSE_SMALL_NZ) when all of it fits in
-// shared memory and the FP32 spectral array fits in half the L2: there the
-// separate passes are bound by latency rather than by HBM, and the column
-// gathers (8 of every 32 bytes of a sector) are served from L2. With one
-// block of up to 227 KB per SM the kernel is itself latency-bound, and on
-// GB300 it does not beat the separate passes.
+// warp-partitioned one. Taken when all of it fits in shared memory and the
+// FP32 spectral array fits in half the L2 (there the separate passes are
+// bound by latency rather than by HBM, and the column gathers, 8 of every 32
+// bytes of a sector, are served from L2), by default only for nz ny <= 8192
+// and ny <= 512: with one block of up to 227 KB per SM the kernel is itself
+// latency-bound, and on GB300 it beats the separate passes only on small
+// bricks (measured 1.4-2.1x there, 10% slower at 512 x 512 x 32).
 struct YtLayout {
   size_t brick, tw, piv, lowpiv, lowd, zb, total;  // byte offsets
 };
@@ -1247,7 +1248,9 @@ size_t yfft_thomas32_smem(const Grid& g, int lmax) { return yt_layout(g, lmax).t
 cudaError_t init_yfft_thomas32(afid_ctx* c, int lmax) {
   c->fuse_yt = 0;
   const Grid& g = c->g;
-  if (c->prec != AFID_MIXED || !(c->flags & AFID_FUSE_SMALL_NZ) || g.ny < 8) return cudaSuccess;
+  if (c->prec != AFID_MIXED || (c->flags & AFID_NO_FUSE) || g.ny < 8) return cudaSuccess;
+  // by default only where it was measured faster than the separate passes
+  if (!(c->flags & AFID_FUSE_SMALL_NZ) && ((long long)g.nz * g.ny > 8192 || g.ny > 512)) return cudaSuccess;
   int smem_optin = 0, l2 = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);

@@ -193,12 +193,12 @@ def test_rb_conduction_steady_gpu():
     assert float((S[3] - T0).abs().max()) < 1e-13
 
 
-@pytest.mark.parametrize("fuse", [True, False])
+@pytest.mark.parametrize("fuse", [True, False, None])
 @pytest.mark.parametrize("shape", [(64, 64, 33), (128, 32, 48)])
 def test_mixed_poisson(shape, fuse):
     """fuse: the small-nz kernel that runs the y transforms and the wall-normal
-    solves of one kx column in shared memory (these grids qualify), or the
-    separate passes."""
+    solves of one kx column in shared memory (these grids qualify), the
+    separate passes, or the context's own choice."""
     nx, ny, nz = shape
     w = synth.workload("pc64", nx=nx, ny=ny, nz=nz)
     g = ogrid(w)
@@ -334,7 +334,7 @@ def test_mixed_fused_small_nz_matches_separate_passes(shape):
     a, ia = fused.poisson_solve(gpu(b), info=True)
     fams = fused.profile_read()
     assert fams["yfft_thomas"][1] >= 1 and fams["thomas"][1] == 0     # the fused kernel ran
-    p, ip = make_ctx(w, **kw).poisson_solve(gpu(b), info=True)
+    p, ip = make_ctx(w, fuse=False, **kw).poisson_solve(gpu(b), info=True)
     torch.cuda.synchronize()
     assert ia["status"] in (0, 5) and ip["status"] in (0, 5)
     assert rel_l2(a, p) < 1e-11
