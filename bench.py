@@ -194,25 +194,30 @@ def family_work(fam: str, w):
     return None
 
 
-def src_hash():
+# the translation unit holding each captured kernel family
+FAMILY_SOURCE = {"r2c_x": "k_spectral.cu", "fft_y": "k_spectral.cu", "thomas": "k_spectral.cu",
+                 "zero_mode": "k_spectral.cu", "c2r_x": "k_spectral.cu", "project": "k_physical.cu",
+                 "crank_nicolson": "k_physical.cu", "cn_tables": "k_physical.cu", "rhs": "k_rhs.cu"}
+
+
+def src_hash(fam: str) -> str:
+    """Hash of the sources a family's kernels are compiled from: its translation
+    unit and the two internal headers every kernel includes."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1705_01423_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in (FAMILY_SOURCE[fam], "afid_internal.cuh", "fft.cuh"):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def traffic_for(fam: str, w):
     """DRAM bytes per launch group from the committed ncu summary, scaled to the
-    workload; None when missing or taken on different kernel sources."""
+    workload; None when missing or taken on different sources of that family."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or fam not in FAMILY_SOURCE:
         return None
-    d = json.load(open(p))
-    if d.get("src_hash") != src_hash():
-        return None
-    e = d.get("families", {}).get(fam)
-    if not e:
+    e = json.load(open(p)).get("families", {}).get(fam)
+    if not e or e.get("src_hash") != src_hash(fam):
         return None
     return e["bytes_per_point"] * w.nx * w.ny * w.nz
 
