@@ -162,91 +162,105 @@ __global__ void __launch_bounds__(128) k_adj_explicit(Grid g, Metric m, PhysA ph
   // ------------------------------------------------------------ u equation
   {
     const double Z = -Zu[c];  // H_u = -(ax + ay + az) + nu lap
+    // Z times the stencil factors, formed once, with the 1/2 of each two-point
+    // average folded in (the sums below are twice the forward stencil's
+    // averages): each contribution is then one multiply. The FP64 pipe bounds
+    // this kernel; the atomics' additions happen in L2.
+    const double Zx = Z * hx, Zy = Z * (0.5 * hy), Zz = Z * (0.5 * hz);
     const double u0 = u[c], uip = u[cip], uim = u[cim], ujp = u[cjp], ujm = u[cjm];
-    const double ur = 0.5 * (u0 + uip), ul = 0.5 * (uim + u0);
-    aadd(gu, cip, Z * ur * rdx);
-    aadd(gu, c, Z * (ur - ul) * rdx);
-    aadd(gu, cim, -Z * ul * rdx);
-    const double Vj = 0.5 * (v[cim] + v[c]), Uj = 0.5 * (ujm + u0);
-    const double Vjp = 0.5 * (v[ix(g, k, jp, im)] + v[cjp]), Ujp = 0.5 * (u0 + ujp);
-    aadd(gv, ix(g, k, jp, im), Z * Ujp * hy);
-    aadd(gv, cjp, Z * Ujp * hy);
-    aadd(gv, cim, -Z * Uj * hy);
-    aadd(gv, c, -Z * Uj * hy);
-    aadd(gu, cjp, Z * Vjp * hy);
-    aadd(gu, c, Z * (Vjp - Vj) * hy);
-    aadd(gu, cjm, -Z * Vj * hy);
+    const double ur = u0 + uip, ul = uim + u0;
+    aadd(gu, cip, Zx * ur);
+    aadd(gu, c, Zx * (ur - ul));
+    aadd(gu, cim, -Zx * ul);
+    const double Vj = v[cim] + v[c], Uj = ujm + u0;
+    const double Vjp = v[ix(g, k, jp, im)] + v[cjp], Ujp = u0 + ujp;
+    const double ZUjp = Zy * Ujp, ZUj = Zy * Uj;
+    aadd(gv, ix(g, k, jp, im), ZUjp);
+    aadd(gv, cjp, ZUjp);
+    aadd(gv, cim, -ZUj);
+    aadd(gv, c, -ZUj);
+    aadd(gu, cjp, Zy * Vjp);
+    aadd(gu, c, Zy * (Vjp - Vj));
+    aadd(gu, cjm, -Zy * Vj);
     if (k > 0) {
-      const double Wk = 0.5 * (w[cim] + w[c]), Uk = 0.5 * (u[c - NXY] + u0);
-      aadd(gw, cim, -Z * Uk * hz);
-      aadd(gw, c, -Z * Uk * hz);
-      aadd(gu, c - NXY, -Z * Wk * hz);
-      aadd(gu, c, -Z * Wk * hz);
+      const double Wk = w[cim] + w[c], Uk = u[c - NXY] + u0;
+      const double ZUk = Zz * Uk, ZWk = Zz * Wk;
+      aadd(gw, cim, -ZUk);
+      aadd(gw, c, -ZUk);
+      aadd(gu, c - NXY, -ZWk);
+      aadd(gu, c, -ZWk);
     }
     if (k < nz - 1) {
-      const double Wk1 = 0.5 * (w[cim + NXY] + w[c + NXY]), Uk1 = 0.5 * (u0 + u[c + NXY]);
-      aadd(gw, cim + NXY, Z * Uk1 * hz);
-      aadd(gw, c + NXY, Z * Uk1 * hz);
-      aadd(gu, c + NXY, Z * Wk1 * hz);
-      aadd(gu, c, Z * Wk1 * hz);
+      const double Wk1 = w[cim + NXY] + w[c + NXY], Uk1 = u0 + u[c + NXY];
+      const double ZUk1 = Zz * Uk1, ZWk1 = Zz * Wk1;
+      aadd(gw, cim + NXY, ZUk1);
+      aadd(gw, c + NXY, ZUk1);
+      aadd(gu, c + NXY, ZWk1);
+      aadd(gu, c, ZWk1);
     }
     const double Zl = Zu[c] * ph.nu;
-    aadd(gu, cip, Zl * g.rdx2);
-    aadd(gu, cim, Zl * g.rdx2);
-    aadd(gu, cjp, Zl * g.rdy2);
-    aadd(gu, cjm, Zl * g.rdy2);
-    aadd(gu, c, -2.0 * Zl * (g.rdx2 + g.rdy2));
+    const double Zlx = Zl * g.rdx2, Zly = Zl * g.rdy2;
+    aadd(gu, cip, Zlx);
+    aadd(gu, cim, Zlx);
+    aadd(gu, cjp, Zly);
+    aadd(gu, cjm, Zly);
+    aadd(gu, c, -2.0 * (Zlx + Zly));
     // direct terms: dt alpha (nu dzz u - G_x p)
-    const double r = Ru[c] * da;
-    aadd(gu, c, -r * ph.nu * (m.cc[k] + m.ca[k]));
-    if (k > 0) aadd(gu, c - NXY, r * ph.nu * m.ca[k]);
-    if (k < nz - 1) aadd(gu, c + NXY, r * ph.nu * m.cc[k]);
-    aadd(gp, c, -r * rdx);
-    aadd(gp, cim, r * rdx);
+    const double r = Ru[c] * da, rn = r * ph.nu, rx = r * rdx;
+    aadd(gu, c, -rn * (m.cc[k] + m.ca[k]));
+    if (k > 0) aadd(gu, c - NXY, rn * m.ca[k]);
+    if (k < nz - 1) aadd(gu, c + NXY, rn * m.cc[k]);
+    aadd(gp, c, -rx);
+    aadd(gp, cim, rx);
   }
   // ------------------------------------------------------------ v equation
   {
     const double Z = -Zv[c];
+    const double Zx = Z * (0.5 * hx), Zy = Z * hy, Zz = Z * (0.5 * hz);  // 1/2 folded in
     const double v0 = v[c], vip = v[cip], vim = v[cim], vjp = v[cjp], vjm = v[cjm];
-    const double Uj = 0.5 * (u[cjm] + u[c]), Vj = 0.5 * (vim + v0);
-    const double Uip = 0.5 * (u[ix(g, k, jm, ip)] + u[cip]), Vip = 0.5 * (v0 + vip);
-    aadd(gu, ix(g, k, jm, ip), Z * Vip * hx);
-    aadd(gu, cip, Z * Vip * hx);
-    aadd(gu, cjm, -Z * Vj * hx);
-    aadd(gu, c, -Z * Vj * hx);
-    aadd(gv, cip, Z * Uip * hx);
-    aadd(gv, c, Z * (Uip - Uj) * hx);
-    aadd(gv, cim, -Z * Uj * hx);
-    const double vt = 0.5 * (v0 + vjp), vb = 0.5 * (vjm + v0);
-    aadd(gv, cjp, Z * vt * rdy);
-    aadd(gv, c, Z * (vt - vb) * rdy);
-    aadd(gv, cjm, -Z * vb * rdy);
+    const double Uj = u[cjm] + u[c], Vj = vim + v0;
+    const double Uip = u[ix(g, k, jm, ip)] + u[cip], Vip = v0 + vip;
+    const double ZVip = Zx * Vip, ZVj = Zx * Vj;
+    aadd(gu, ix(g, k, jm, ip), ZVip);
+    aadd(gu, cip, ZVip);
+    aadd(gu, cjm, -ZVj);
+    aadd(gu, c, -ZVj);
+    aadd(gv, cip, Zx * Uip);
+    aadd(gv, c, Zx * (Uip - Uj));
+    aadd(gv, cim, -Zx * Uj);
+    const double vt = v0 + vjp, vb = vjm + v0;
+    aadd(gv, cjp, Zy * vt);
+    aadd(gv, c, Zy * (vt - vb));
+    aadd(gv, cjm, -Zy * vb);
     if (k > 0) {
-      const double Wk = 0.5 * (w[cjm] + w[c]), Vk = 0.5 * (v[c - NXY] + v0);
-      aadd(gw, cjm, -Z * Vk * hz);
-      aadd(gw, c, -Z * Vk * hz);
-      aadd(gv, c - NXY, -Z * Wk * hz);
-      aadd(gv, c, -Z * Wk * hz);
+      const double Wk = w[cjm] + w[c], Vk = v[c - NXY] + v0;
+      const double ZVk = Zz * Vk, ZWk = Zz * Wk;
+      aadd(gw, cjm, -ZVk);
+      aadd(gw, c, -ZVk);
+      aadd(gv, c - NXY, -ZWk);
+      aadd(gv, c, -ZWk);
     }
     if (k < nz - 1) {
-      const double Wk1 = 0.5 * (w[cjm + NXY] + w[c + NXY]), Vk1 = 0.5 * (v0 + v[c + NXY]);
-      aadd(gw, cjm + NXY, Z * Vk1 * hz);
-      aadd(gw, c + NXY, Z * Vk1 * hz);
-      aadd(gv, c + NXY, Z * Wk1 * hz);
-      aadd(gv, c, Z * Wk1 * hz);
+      const double Wk1 = w[cjm + NXY] + w[c + NXY], Vk1 = v0 + v[c + NXY];
+      const double ZVk1 = Zz * Vk1, ZWk1 = Zz * Wk1;
+      aadd(gw, cjm + NXY, ZVk1);
+      aadd(gw, c + NXY, ZVk1);
+      aadd(gv, c + NXY, ZWk1);
+      aadd(gv, c, ZWk1);
     }
     const double Zl = Zv[c] * ph.nu;
-    aadd(gv, cip, Zl * g.rdx2);
-    aadd(gv, cim, Zl * g.rdx2);
-    aadd(gv, cjp, Zl * g.rdy2);
-    aadd(gv, cjm, Zl * g.rdy2);
-    aadd(gv, c, -2.0 * Zl * (g.rdx2 + g.rdy2));
-    const double r = Rv[c] * da;
-    aadd(gv, c, -r * ph.nu * (m.cc[k] + m.ca[k]));
-    if (k > 0) aadd(gv, c - NXY, r * ph.nu * m.ca[k]);
-    if (k < nz - 1) aadd(gv, c + NXY, r * ph.nu * m.cc[k]);
-    aadd(gp, c, -r * rdy);
-    aadd(gp, cjm, r * rdy);
+    const double Zlx = Zl * g.rdx2, Zly = Zl * g.rdy2;
+    aadd(gv, cip, Zlx);
+    aadd(gv, cim, Zlx);
+    aadd(gv, cjp, Zly);
+    aadd(gv, cjm, Zly);
+    aadd(gv, c, -2.0 * (Zlx + Zly));
+    const double r = Rv[c] * da, rn = r * ph.nu, ry = r * rdy;
+    aadd(gv, c, -rn * (m.cc[k] + m.ca[k]));
+    if (k > 0) aadd(gv, c - NXY, rn * m.ca[k]);
+    if (k < nz - 1) aadd(gv, c + NXY, rn * m.cc[k]);
+    aadd(gp, c, -ry);
+    aadd(gp, cjm, ry);
   }
   if (k == 0) return;
   // ------------------------------------------------------------ w and T on face k
@@ -261,80 +275,84 @@ __global__ void __launch_bounds__(128) k_adj_explicit(Grid g, Metric m, PhysA ph
   const bool up_int = k + 1 <= nz - 1, dn_int = k - 1 >= 1;  // neighbouring faces interior?
   {
     const double Z = -Zw[c];
+    const double Zhx = Z * hx, Zhy = Z * hy, Zzf = Z * rdzf;
     const double wip = w[cip], wim = w[cim], wjp = w[cjp], wjm = w[cjm];
     // x: (ufip (w0+wip)/2 - ufi (wim+w0)/2)/dx
-    const double a1 = Z * 0.5 * (w0 + wip) * rdx, a0 = -Z * 0.5 * (wim + w0) * rdx;
+    const double a1 = Zhx * (w0 + wip), a0 = -Zhx * (wim + w0);
     aadd(gu, cipkm, a1 * wlo);
     aadd(gu, cip, a1 * whi);
     aadd(gu, ckm, a0 * wlo);
     aadd(gu, c, a0 * whi);
-    aadd(gw, cip, Z * ufip * hx);
-    aadd(gw, c, Z * (ufip - ufi) * hx);
-    aadd(gw, cim, -Z * ufi * hx);
-    const double b1 = Z * 0.5 * (w0 + wjp) * rdy, b0 = -Z * 0.5 * (wjm + w0) * rdy;
+    aadd(gw, cip, Zhx * ufip);
+    aadd(gw, c, Zhx * (ufip - ufi));
+    aadd(gw, cim, -Zhx * ufi);
+    const double b1 = Zhy * (w0 + wjp), b0 = -Zhy * (wjm + w0);
     aadd(gv, cjpkm, b1 * wlo);
     aadd(gv, cjp, b1 * whi);
     aadd(gv, ckm, b0 * wlo);
     aadd(gv, c, b0 * whi);
-    aadd(gw, cjp, Z * vfjp * hy);
-    aadd(gw, c, Z * (vfjp - vfj) * hy);
-    aadd(gw, cjm, -Z * vfj * hy);
+    aadd(gw, cjp, Zhy * vfjp);
+    aadd(gw, c, Zhy * (vfjp - vfj));
+    aadd(gw, cjm, -Zhy * vfj);
     // z: (wc_k^2 - wc_km^2)/dzf
-    if (up_int) aadd(gw, c + NXY, Z * wc_k * rdzf);
-    aadd(gw, c, Z * (wc_k - wc_km) * rdzf);
-    if (dn_int) aadd(gw, ckm, -Z * wc_km * rdzf);
+    if (up_int) aadd(gw, c + NXY, Zzf * wc_k);
+    aadd(gw, c, Zzf * (wc_k - wc_km));
+    if (dn_int) aadd(gw, ckm, -Zzf * wc_km);
     const double Zl = Zw[c] * ph.nu;
-    aadd(gw, cip, Zl * g.rdx2);
-    aadd(gw, cim, Zl * g.rdx2);
-    aadd(gw, cjp, Zl * g.rdy2);
-    aadd(gw, cjm, Zl * g.rdy2);
-    aadd(gw, c, -2.0 * Zl * (g.rdx2 + g.rdy2));
+    const double Zlx = Zl * g.rdx2, Zly = Zl * g.rdy2;
+    aadd(gw, cip, Zlx);
+    aadd(gw, cim, Zlx);
+    aadd(gw, cjp, Zly);
+    aadd(gw, cjm, Zly);
+    aadd(gw, c, -2.0 * (Zlx + Zly));
     if (T) aadd(gT, c, Zw[c] * ph.buoy);
-    const double r = Rw[c] * da;
-    aadd(gw, c, -r * ph.nu * (m.fc[k] + m.fa[k]));
-    if (dn_int) aadd(gw, ckm, r * ph.nu * m.fa[k]);
-    if (up_int) aadd(gw, c + NXY, r * ph.nu * m.fc[k]);
-    aadd(gp, c, -r * rdzf);
-    aadd(gp, ckm, r * rdzf);
+    const double r = Rw[c] * da, rn = r * ph.nu, rz = r * rdzf;
+    aadd(gw, c, -rn * (m.fc[k] + m.fa[k]));
+    if (dn_int) aadd(gw, ckm, rn * m.fa[k]);
+    if (up_int) aadd(gw, c + NXY, rn * m.fc[k]);
+    aadd(gp, c, -rz);
+    aadd(gp, ckm, rz);
   }
   if (T) {
     const double Z = -ZT[c];
+    const double Zhx = Z * hx, Zhy = Z * hy, Zhzf = Z * (0.5 * rdzf);
     const double t0 = T[c], tip = T[cip], tim = T[cim], tjp = T[cjp], tjm = T[cjm];
     const double tk1 = T[c + NXY], tkm = T[ckm];
-    const double a1 = Z * 0.5 * (t0 + tip) * rdx, a0 = -Z * 0.5 * (tim + t0) * rdx;
+    const double a1 = Zhx * (t0 + tip), a0 = -Zhx * (tim + t0);
     aadd(gu, cipkm, a1 * wlo);
     aadd(gu, cip, a1 * whi);
     aadd(gu, ckm, a0 * wlo);
     aadd(gu, c, a0 * whi);
-    aadd(gT, cip, Z * ufip * hx);
-    aadd(gT, c, Z * (ufip - ufi) * hx);
-    aadd(gT, cim, -Z * ufi * hx);
-    const double b1 = Z * 0.5 * (t0 + tjp) * rdy, b0 = -Z * 0.5 * (tjm + t0) * rdy;
+    aadd(gT, cip, Zhx * ufip);
+    aadd(gT, c, Zhx * (ufip - ufi));
+    aadd(gT, cim, -Zhx * ufi);
+    const double b1 = Zhy * (t0 + tjp), b0 = -Zhy * (tjm + t0);
     aadd(gv, cjpkm, b1 * wlo);
     aadd(gv, cjp, b1 * whi);
     aadd(gv, ckm, b0 * wlo);
     aadd(gv, c, b0 * whi);
-    aadd(gT, cjp, Z * vfjp * hy);
-    aadd(gT, c, Z * (vfjp - vfj) * hy);
-    aadd(gT, cjm, -Z * vfj * hy);
+    aadd(gT, cjp, Zhy * vfjp);
+    aadd(gT, c, Zhy * (vfjp - vfj));
+    aadd(gT, cjm, -Zhy * vfj);
     // z: (wc_k (t0+tk1)/2 - wc_km (tkm+t0)/2)/dzf
-    const double hzf = 0.5 * rdzf;
-    if (up_int) aadd(gw, c + NXY, Z * 0.5 * (t0 + tk1) * hzf);
-    aadd(gw, c, Z * (0.5 * (t0 + tk1) - 0.5 * (tkm + t0)) * hzf);
-    if (dn_int) aadd(gw, ckm, -Z * 0.5 * (tkm + t0) * hzf);
-    if (up_int) aadd(gT, c + NXY, Z * wc_k * hzf);
-    aadd(gT, c, Z * (wc_k - wc_km) * hzf);
-    if (dn_int) aadd(gT, ckm, -Z * wc_km * hzf);
+    const double tc_k = 0.5 * (t0 + tk1), tc_km = 0.5 * (tkm + t0);
+    if (up_int) aadd(gw, c + NXY, Zhzf * tc_k);
+    aadd(gw, c, Zhzf * (tc_k - tc_km));
+    if (dn_int) aadd(gw, ckm, -Zhzf * tc_km);
+    if (up_int) aadd(gT, c + NXY, Zhzf * wc_k);
+    aadd(gT, c, Zhzf * (wc_k - wc_km));
+    if (dn_int) aadd(gT, ckm, -Zhzf * wc_km);
     const double Zl = ZT[c] * ph.kappa;
-    aadd(gT, cip, Zl * g.rdx2);
-    aadd(gT, cim, Zl * g.rdx2);
-    aadd(gT, cjp, Zl * g.rdy2);
-    aadd(gT, cjm, Zl * g.rdy2);
-    aadd(gT, c, -2.0 * Zl * (g.rdx2 + g.rdy2));
-    const double r = RT[c] * da;
-    aadd(gT, c, -r * ph.kappa * (m.fc[k] + m.fa[k]));
-    if (dn_int) aadd(gT, ckm, r * ph.kappa * m.fa[k]);
-    if (up_int) aadd(gT, c + NXY, r * ph.kappa * m.fc[k]);
+    const double Zlx = Zl * g.rdx2, Zly = Zl * g.rdy2;
+    aadd(gT, cip, Zlx);
+    aadd(gT, cim, Zlx);
+    aadd(gT, cjp, Zly);
+    aadd(gT, cjm, Zly);
+    aadd(gT, c, -2.0 * (Zlx + Zly));
+    const double r = RT[c] * da, rk = r * ph.kappa;
+    aadd(gT, c, -rk * (m.fc[k] + m.fa[k]));
+    if (dn_int) aadd(gT, ckm, rk * m.fa[k]);
+    if (up_int) aadd(gT, c + NXY, rk * m.fc[k]);
   }
 }
 
