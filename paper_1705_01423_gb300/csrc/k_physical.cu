@@ -393,11 +393,15 @@ __global__ void k_cn_sweep(Grid g, const double* __restrict__ tab, double* R0, d
       dp = (R[k * NXY + col] - sub[k] * dp) * mm[k];
       R[k * NXY + col] = dp;
     }
+    // q += x is issued as an atomic addition (each location is updated once, by
+    // this thread, so the result is that of the plain addition): the addition
+    // is done in L2, off the FP64 pipe that bounds this sweep, and q is not
+    // loaded by the SM
     double x = dp;
-    q[k1 * NXY + col] += x;
+    atomicAdd(q + k1 * NXY + col, x);
     for (int k = k1 - 1; k >= k0; --k) {
       x = R[k * NXY + col] - cp[k] * x;
-      q[k * NXY + col] += x;
+      atomicAdd(q + k * NXY + col, x);
     }
   } else {
     double z = q[k0 * NXY + col] * mm[k0];
