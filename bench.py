@@ -169,9 +169,10 @@ def family_work(fam: str, w):
       thomas 7 per complex point (4 forward, 3 backward)
       project 9; rhs 108 (shared face fluxes 29, u 19, v 19, w 21, T 17, per-plane
       factors 3; the recomputed fluxes of the warp- and block-edge neighbours are
-      overhead, not counted); crank_nicolson 12 (4 fields: 2 forward-elimination
-      and 1 back-substitution operations each on the FP64 pipe; the q += dq
-      addition is an atomic done in L2);
+      overhead, not counted); crank_nicolson 8 (4 fields: one forward-elimination
+      FMA, the reciprocal pivot being folded into the right-hand side the
+      explicit-terms kernel writes, and one back-substitution FMA each on the
+      FP64 pipe; the q += dq addition is an atomic done in L2);
       cfl_reduce 7 (|.| is an operand modifier)."""
     nx, ny, nz = w.nx, w.ny, w.nz
     n = nx * ny * nz
@@ -190,7 +191,7 @@ def family_work(fam: str, w):
     if fam == "rhs":
         return 136 * n, 108 * n
     if fam == "crank_nicolson":
-        return 4 * 24 * n, 12 * n
+        return 4 * 24 * n, 8 * n
     if fam == "cfl_reduce":
         return 24 * n, 7 * n
     return None

@@ -83,8 +83,18 @@ struct Prof {
 // Arrays per variable set in the Crank-Nicolson table (k_cn_tables): sub,
 // m, c', sup, and the explicit-side coefficients 2 beta a, 2 beta c,
 // -2 beta (a + c); set 0 also carries the per-plane factors of the explicit
-// terms: alpha_l dt / dzf, dzc^-1 / 4, dzf^-1 / 4 (arrays 7, 8, 9).
-constexpr int CN_TAB_ARRAYS = 10;
+// terms: alpha_l dt / dzf, dzc^-1 / 4, dzf^-1 / 4 (arrays 7, 8, 9). Arrays
+// 10-17 are the same coefficients multiplied by the row's reciprocal pivot
+// m_k, so that the explicit-terms kernels write m_k R_k directly and the
+// forward elimination is d'_k = m_k R_k - (m_k sub_k) d'_{k-1}: 10 m sub,
+// 11-13 m times arrays 4-6, 14 m dt gamma_l, 15 m dt rho_l, 16 the pressure
+// gradient factor times m (set 0: alpha_l dt / dx; set 1: alpha_l dt / dzf_k),
+// 17 (set 0) m alpha_l dt / dy.
+constexpr int CN_TAB_ARRAYS = 18;
+enum CnTab {
+  CN_SUB = 0, CN_M, CN_CP, CN_SUP, CN_EA, CN_EC, CN_ED, CN_PZ, CN_QZ, CN_QZF,
+  CN_MSUB, CN_MEA, CN_MEC, CN_MED, CN_MCG, CN_MCR, CN_MGX, CN_MGY
+};
 
 struct Grid {
   int nx, ny, nz;

@@ -245,13 +245,17 @@ __global__ void __launch_bounds__(256) k_mr_scalar_rhs(Grid g, Metric m, double 
   const size_t cip = (size_t)j * nx + ip, cim = (size_t)j * nx + im;
   const size_t cjp = (size_t)jp * nx + i, cjm = (size_t)jm * nx + i;
   const int L = nz + 1;
-  const double cg = dt * rk_gamma(l), cr = dt * rk_rho(l);
+  // R is written multiplied by the reciprocal pivot of its Crank-Nicolson row:
+  // the coefficients come pre-scaled per plane (set 2 of the fine-grid table)
+  const double* __restrict__ mcg = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MCG) * L;
+  const double* __restrict__ mcr = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MCR) * L;
+  (void)dt;
   const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
   const double lap0 = 2.0 * (g.rdx2 + g.rdy2);
-  const double* __restrict__ ea = cnt + (size_t)(2 * CN_TAB_ARRAYS + 4) * L;  // alpha dt kappa dzz
+  const double* __restrict__ ea = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MEA) * L;  // m alpha dt kappa dzz
   const double* __restrict__ ec = ea + L;
   const double* __restrict__ ed = ec + L;
-  const double* __restrict__ qzf = cnt + (size_t)9 * L;  // dzf^-1 / 4
+  const double* __restrict__ qzf = cnt + (size_t)CN_QZF * L;  // dzf^-1 / 4
 
   const int kb = blockIdx.z * kchunk;
   const int k0 = max(1, kb), k1 = min(nz, kb + kchunk);
@@ -281,8 +285,8 @@ __global__ void __launch_bounds__(256) k_mr_scalar_rhs(Grid g, Metric m, double 
     const double lap = fma(-lap0, t0, fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2));
     const double H = fma(kappa, lap, -A);
     const double z = fma(ea[k], tkm, fma(ec[k], tk1, ed[k] * t0));
-    double r = fma(cg, H, z);
-    if (l > 0) r = fma(cr, HT[c + col], r);
+    double r = fma(mcg[k], H, z);
+    if (l > 0) r = fma(mcr[k], HT[c + col], r);
     HT[c + col] = H;
     RT[c + col] = r;
     ukm = uk;
@@ -322,13 +326,17 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_mr_scalar_rhs_sh(
   const size_t cip = (size_t)j * nx + ip, cim = (size_t)j * nx + im;
   const size_t cjp = (size_t)jp * nx + i, cjm = (size_t)jm * nx + i;
   const int L = nz + 1;
-  const double cg = dt * rk_gamma(l), cr = dt * rk_rho(l);
+  // R is written multiplied by the reciprocal pivot of its Crank-Nicolson row:
+  // the coefficients come pre-scaled per plane (set 2 of the fine-grid table)
+  const double* __restrict__ mcg = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MCG) * L;
+  const double* __restrict__ mcr = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MCR) * L;
+  (void)dt;
   const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
   const double lap0 = 2.0 * (g.rdx2 + g.rdy2);
-  const double* __restrict__ ea = cnt + (size_t)(2 * CN_TAB_ARRAYS + 4) * L;
+  const double* __restrict__ ea = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MEA) * L;
   const double* __restrict__ ec = ea + L;
   const double* __restrict__ ed = ec + L;
-  const double* __restrict__ qzf = cnt + (size_t)9 * L;
+  const double* __restrict__ qzf = cnt + (size_t)CN_QZF * L;
   const bool last_x = tx == BX - 1, last_row = ty == BY - 1;
   __shared__ double sfy[2][BY][BX];  // lower-face y flux of every thread
   __shared__ double sfx[2][BY];      // left-face x flux of x = 32 (second warp of a row)
@@ -372,8 +380,8 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_mr_scalar_rhs_sh(
     const double lap = fma(-lap0, t0, fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2));
     const double H = fma(kappa, lap, -A);
     const double z = fma(ea[k], tkm, fma(ec[k], tk1, ed[k] * t0));
-    double r = fma(cg, H, z);
-    if (l > 0) r = fma(cr, HT[c + col], r);
+    double r = fma(mcg[k], H, z);
+    if (l > 0) r = fma(mcr[k], HT[c + col], r);
     HT[c + col] = H;
     RT[c + col] = r;
     ukm = uk;

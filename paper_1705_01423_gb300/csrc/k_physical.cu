@@ -348,10 +348,25 @@ __global__ void __launch_bounds__(96) k_cn_tables(Grid g, Metric m, int l, doubl
     }
   }
   __syncwarp();
+  const double adt = rk_alpha(l) * dt, gdt = rk_gamma(l) * dt, rdt = rk_rho(l) * dt;
+  double* const base = tab + (size_t)o * CN_TAB_ARRAYS * L;
   for (int k = k0 + lane; k < k1; k += 32) {
     const double mk = mm[k] / cp[k];
     mm[k] = mk;
     cp[k] = sp[k] * mk;
+    // the coefficients of the right-hand side scaled by the reciprocal pivot
+    base[CN_MSUB * L + k] = mk * sub[k];
+    base[CN_MEA * L + k] = mk * ea[k];
+    base[CN_MEC * L + k] = mk * ec[k];
+    base[CN_MED * L + k] = mk * ed[k];
+    base[CN_MCG * L + k] = mk * gdt;
+    base[CN_MCR * L + k] = mk * rdt;
+    if (o == 0) {
+      base[CN_MGX * L + k] = mk * (adt * g.rdx);
+      base[CN_MGY * L + k] = mk * (adt * g.rdy);
+    } else if (o == 1) {
+      base[CN_MGX * L + k] = mk * (adt * m.rdzf[k]);
+    }
   }
 }
 
@@ -387,10 +402,12 @@ __global__ void k_cn_sweep(Grid g, const double* __restrict__ tab, double* R0, d
   const double* sp = cp + L;
   const int k0 = var < 2 ? 0 : 1, k1 = g.nz - 1;  // inclusive range
   if (!ADJ) {
-    double dp = R[k0 * NXY + col] * mm[k0];
-    R[k0 * NXY + col] = dp;
+    // R holds m_k R_k (the explicit-terms kernels scale it): d'_k0 = R_k0 and
+    // d'_k = R_k - (m_k sub_k) d'_{k-1}, one FMA per row
+    const double* msub = sub + (size_t)CN_MSUB * L;
+    double dp = R[k0 * NXY + col];
     for (int k = k0 + 1; k <= k1; ++k) {
-      dp = (R[k * NXY + col] - sub[k] * dp) * mm[k];
+      dp = fma(-msub[k], dp, R[k * NXY + col]);
       R[k * NXY + col] = dp;
     }
     // q += x is issued as an atomic addition (each location is updated once, by

@@ -65,13 +65,16 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
   const bool first_lane = tx == 0, last_lane = tx == BX - 1;
   const bool first_row = ty == 0, last_row = ty == BY - 1;
 
-  const double dt = dt_in > 0.0 ? dt_in : scal[S_DT];
-  const double cg = dt * rk_gamma(l), cr = dt * rk_rho(l), ca_ = dt * rk_alpha(l);
-  const double cpx = ca_ * g.rdx, cpy = ca_ * g.rdy;
-  // alpha_l dt d dzz coefficients of this substep (k_cn_tables): cells (nu),
-  // faces (nu), faces (kappa); q_{k-1}, q_{k+1} and q_k weights
-  // (read as cnt[(set * CN_TAB_ARRAYS + 4..6) * L + k]; one base pointer keeps
-  // the register count down)
+  // The right-hand sides are written multiplied by the reciprocal pivot m_k of
+  // their Crank-Nicolson row (the sweep's forward elimination then needs no
+  // multiply): every coefficient of R -- dt gamma_l, dt rho_l, the
+  // alpha_l dt d dzz weights of q_{k-1}, q_{k+1}, q_k and the pressure-gradient
+  // factors -- comes pre-scaled per plane from the substep's table (k_cn_tables,
+  // cells / faces (nu) / faces (kappa); read as cnt[(set * CN_TAB_ARRAYS + a) * L
+  // + k], one base pointer keeping the register count down). dt itself enters
+  // only through those tables.
+  (void)dt_in;
+  (void)scal;
   const int L = nz + 1;
   // this block's range of k (the z-march is split into chunks for load balance)
   const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
@@ -223,14 +226,14 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
     }
 
     // ---------------------------------------------------------------- u, v at cell k
-    const double qz = cnt[8 * L + k];  // dzc^-1 / 4
+    const double qz = cnt[CN_QZ * L + k];  // dzc^-1 / 4
     {
       const double A = fma(fzu1 - fzu, qz, fma(Cjp - C, qy, (fxu - fxum) * qx));
       const double lap = fma(-lap0, u0, fma(ujp + ujm, g.rdy2, (uip + uim) * g.rdx2));
       const double H = fma(ph.nu, lap, -A);
-      const double z = fma(cnt[4 * L + k], ukm, fma(cnt[5 * L + k], ukp, fma(cnt[6 * L + k], u0, -cpx * (p0 - p[c + cim]))));
-      double r = fma(cg, H, z);
-      if (l > 0) r = fma(cr, Hu[c + col], r);
+      const double z = fma(cnt[CN_MEA * L + k], ukm, fma(cnt[CN_MEC * L + k], ukp, fma(cnt[CN_MED * L + k], u0, -cnt[CN_MGX * L + k] * (p0 - p[c + cim]))));
+      double r = fma(cnt[CN_MCG * L + k], H, z);
+      if (l > 0) r = fma(cnt[CN_MCR * L + k], Hu[c + col], r);
       Hu[c + col] = H;
       Ru[c + col] = r;
     }
@@ -238,9 +241,9 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
       const double A = fma(fzv1 - fzv, qz, fma(fyv - fyvm, qy, (Cip - C) * qx));
       const double lap = fma(-lap0, v0, fma(vjp + vjm, g.rdy2, (vip + vim) * g.rdx2));
       const double H = fma(ph.nu, lap, -A);
-      const double z = fma(cnt[4 * L + k], vkm, fma(cnt[5 * L + k], vkp, fma(cnt[6 * L + k], v0, -cpy * (p0 - p[c + cjm]))));
-      double r = fma(cg, H, z);
-      if (l > 0) r = fma(cr, Hv[c + col], r);
+      const double z = fma(cnt[CN_MEA * L + k], vkm, fma(cnt[CN_MEC * L + k], vkp, fma(cnt[CN_MED * L + k], v0, -cnt[CN_MGY * L + k] * (p0 - p[c + cjm]))));
+      double r = fma(cnt[CN_MCG * L + k], H, z);
+      if (l > 0) r = fma(cnt[CN_MCR * L + k], Hv[c + col], r);
       Hv[c + col] = H;
       Rv[c + col] = r;
     }
@@ -253,15 +256,15 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
         HT[(size_t)nz * NXY + col] = 0.0;
       }
     } else {
-      const double qzf = cnt[9 * L + k];  // dzf^-1 / 4
+      const double qzf = cnt[CN_QZF * L + k];  // dzf^-1 / 4
       {
         const double A = fma(fzw1 - fzw, qzf, fma(fyw1 - fyw, hy, (fxw1 - fxw) * hx));
         const double lap = fma(-lap0, w0, fma(wjp + wjm0, g.rdy2, (wip + wim0) * g.rdx2));
         double H = fma(ph.nu, lap, -A);
         if (BUOY) H = fma(ph.buoy, t0, H);
-        const double z = fma(cnt[(CN_TAB_ARRAYS + 4) * L + k], wkm, fma(cnt[(CN_TAB_ARRAYS + 5) * L + k], wk1, fma(cnt[(CN_TAB_ARRAYS + 6) * L + k], w0, -cnt[7 * L + k] * (p0 - pkm))));
-        double r = fma(cg, H, z);
-        if (l > 0) r = fma(cr, Hw[c + col], r);
+        const double z = fma(cnt[(CN_TAB_ARRAYS + CN_MEA) * L + k], wkm, fma(cnt[(CN_TAB_ARRAYS + CN_MEC) * L + k], wk1, fma(cnt[(CN_TAB_ARRAYS + CN_MED) * L + k], w0, -cnt[(CN_TAB_ARRAYS + CN_MGX) * L + k] * (p0 - pkm))));
+        double r = fma(cnt[(CN_TAB_ARRAYS + CN_MCG) * L + k], H, z);
+        if (l > 0) r = fma(cnt[(CN_TAB_ARRAYS + CN_MCR) * L + k], Hw[c + col], r);
         Hw[c + col] = H;
         Rw[c + col] = r;
       }
@@ -269,9 +272,9 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
         const double A = fma(fzt1 - fzt, qzf, fma(fyt1 - fyt, hy, (fxt1 - fxt) * hx));
         const double lap = fma(-lap0, t0, fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2));
         const double H = fma(ph.kappa, lap, -A);
-        const double z = fma(cnt[(2 * CN_TAB_ARRAYS + 4) * L + k], tkm, fma(cnt[(2 * CN_TAB_ARRAYS + 5) * L + k], tk1, cnt[(2 * CN_TAB_ARRAYS + 6) * L + k] * t0));
-        double r = fma(cg, H, z);
-        if (l > 0) r = fma(cr, HT[c + col], r);
+        const double z = fma(cnt[(2 * CN_TAB_ARRAYS + CN_MEA) * L + k], tkm, fma(cnt[(2 * CN_TAB_ARRAYS + CN_MEC) * L + k], tk1, cnt[(2 * CN_TAB_ARRAYS + CN_MED) * L + k] * t0));
+        double r = fma(cnt[(2 * CN_TAB_ARRAYS + CN_MCG) * L + k], H, z);
+        if (l > 0) r = fma(cnt[(2 * CN_TAB_ARRAYS + CN_MCR) * L + k], HT[c + col], r);
         HT[c + col] = H;
         RT[c + col] = r;
       }
