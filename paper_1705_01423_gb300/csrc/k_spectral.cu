@@ -264,9 +264,63 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
 //              update is a few 2^-46 of the stencil's terms, i.e. of
 //              |r_{k-1}| times the local condition, far below the FP32
 //              accuracy of the solve it feeds; r_k is stored back.
+//   R32_RESUPD_ST: the same update with the block's stencil footprint staged
+//              in shared memory first (cp.async, every load of the block in
+//              flight at once): the block's rows are lines consecutive j of one
+//              plane (ny a multiple of lines), so it needs the rows j0-1 ..
+//              j0+lines of its plane and j0 .. j0+lines-1 of the planes below and
+//              above, 3 lines + 2 rows of delta; same arithmetic, same results.
+//              Blocks of at most 256 threads, three per SM.
 // R32_RESID and R32_RESUPD store the residual as (head, tail) in rres.
 // Same line transform and unpacking as k_r2c_x.
-enum { R32_FIRST = 0, R32_RESID = 1, R32_RESUPD = 2 };
+enum { R32_FIRST = 0, R32_RESID = 1, R32_RESUPD = 2, R32_RESUPD_ST = 3 };
+
+// float2 words of dynamic shared memory in front of the twiddle table: the
+// lines' transform buffers, which R32_RESUPD_ST lays over its staged rows.
+__host__ __device__ __forceinline__ int r2c32_front_words(int mode, int lines, int nx, int stride) {
+  const int b = lines * stride;
+  if (mode != R32_RESUPD_ST) return b;
+  const int st = ((3 * lines + 2) * nx + 1) / 2;
+  return st > b ? st : b;
+}
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// r - L delta at two neighbouring points (i, i+1) of a row in two-float
+// arithmetic: f = (delta_i, delta_i+1), fw = delta_i-1, fe = delta_i+2, fn / fs
+// the rows j+1 / j-1, fu / fd the planes k+1 / k-1 (used when up / dn), ro the
+// stored residual (head_i, tail_i, head_i+1, tail_i+1); returns the new one.
+__device__ __forceinline__ float4 resupd_pair(float2 f, float fw, float fe, float2 fn, float2 fs, float2 fu,
+                                              float2 fd, bool up, bool dn, float4 ro, float2 ca, float2 cc,
+                                              float2 cd, float xh, float xl, float yh, float yl) {
+  // S = L delta = rdx2 (w + e) + rdy2 (s + n) + pc up + pa down - pdiag centre
+  float sxh = 0.f, sxl = 0.f, syh = 0.f, syl = 0.f;
+  ff_acc(sxh, sxl, -cd.x, -cd.y, f.x);
+  ff_acc(syh, syl, -cd.x, -cd.y, f.y);
+  ff_acc(sxh, sxl, xh, xl, fw);
+  ff_acc(sxh, sxl, xh, xl, f.y);
+  ff_acc(syh, syl, xh, xl, f.x);
+  ff_acc(syh, syl, xh, xl, fe);
+  ff_acc(sxh, sxl, yh, yl, fn.x);
+  ff_acc(sxh, sxl, yh, yl, fs.x);
+  ff_acc(syh, syl, yh, yl, fn.y);
+  ff_acc(syh, syl, yh, yl, fs.y);
+  if (up) {
+    ff_acc(sxh, sxl, cc.x, cc.y, fu.x);
+    ff_acc(syh, syl, cc.x, cc.y, fu.y);
+  }
+  if (dn) {
+    ff_acc(sxh, sxl, ca.x, ca.y, fd.x);
+    ff_acc(syh, syl, ca.x, ca.y, fd.y);
+  }
+  const float2 nx2 = ff_sub(ro.x, ro.y, sxh, sxl);
+  const float2 ny2 = ff_sub(ro.z, ro.w, syh, syl);
+  return make_float4(nx2.x, nx2.y, ny2.x, ny2.y);
+}
 
 // Block sum of one double per thread, valid on thread 0. The values go
 // through shared memory (red: blockDim.x doubles) and only warp 0 adds them:
@@ -285,7 +339,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 }
 
 template <int MODE, bool GEN>
-__global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double* __restrict__ b,
+__global__ void __launch_bounds__(MODE == R32_RESUPD_ST ? 256 : 512, MODE == R32_RESUPD_ST ? 3 : 1) k_r2c_x32(Grid g, Metric m, const double* __restrict__ b,
                                                  const double* __restrict__ phi, float2* __restrict__ spec,
                                                  const float2* __restrict__ tw, double* __restrict__ scal,
                                                  double* __restrict__ part, int stats,
@@ -304,14 +358,72 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
   const bool active = row < nrows;
   const int stride = pad8(M) + 1;
   float2* buf = sm + line * stride;
-  float2* stw = sm + lines * stride;  // twiddle table, nx entries
+  float2* stw = sm + r2c32_front_words(MODE, lines, g.nx, stride);  // twiddle table, nx entries
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
   float fs = 0.f, fc = 0.f, fs2 = 0.f;  // FIRST: compensated FP32 row sum, sum of squares
   float2 zr[8];                         // FIRST: the thread's points, for the first FFT pass
   float rr = 0.f;
   unsigned long long amax = 0ull;
   int k = 0;
-  if (active) {
+  if (MODE == R32_RESUPD_ST) {  // every row of the block is active
+    const int nx = g.nx, q4 = nx >> 2;
+    const int row0 = blockIdx.x * lines;
+    k = row0 / g.ny;
+    const int j0 = row0 - k * g.ny;
+    // staged rows: 0 .. lines+1 plane k at j0-1 .. j0+lines (periodic in y),
+    // lines+2 .. 2 lines+1 plane k-1, 2 lines+2 .. 3 lines+1 plane k+1
+    float* st = reinterpret_cast<float*>(smem_raw);
+    const int nst = (3 * lines + 2) * q4;
+    for (int c = threadIdx.x; c < nst; c += blockDim.x) {
+      const int r = c / q4, q = c - r * q4;
+      int kk = k, jj;
+      if (r < lines + 2) {
+        jj = j0 - 1 + r;
+        jj = jj < 0 ? jj + g.ny : (jj >= g.ny ? jj - g.ny : jj);
+      } else if (r < 2 * lines + 2) {
+        kk = k - 1;
+        jj = j0 + r - (lines + 2);
+      } else {
+        kk = k + 1;
+        jj = j0 + r - (2 * lines + 2);
+      }
+      if (kk < 0 || kk >= g.nz) continue;
+      cp_async16(st + (size_t)r * nx + 4 * q, dprev + ((size_t)kk * g.ny + jj) * nx + 4 * q);
+    }
+    const size_t r0 = (size_t)row * nx;
+    float4 ro[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ro[q] = reinterpret_cast<const float4*>(rres + r0 + 2 * (t + q * T))[0];
+    cp_async_wait_all();
+    __syncthreads();
+    const float2 ca = cff[k], cc = cff[g.nz + k], cd = cff[2 * g.nz + k];
+    const float xh = to_real<float>(g.rdx2), xl = low_part(g.rdx2);
+    const float yh = to_real<float>(g.rdy2), yl = low_part(g.rdy2);
+    const bool up = k < g.nz - 1, dn = k > 0;
+    const float* sc = st + (size_t)(line + 1) * nx;
+    const float* sn = sc + nx;
+    const float* ss = sc - nx;
+    const float* sd = st + (size_t)(lines + 2 + line) * nx;
+    const float* su = st + (size_t)(2 * lines + 2 + line) * nx;
+    float2 val[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = 2 * (t + q * T);
+      const float2 f = *reinterpret_cast<const float2*>(sc + i);
+      const float2 fn = *reinterpret_cast<const float2*>(sn + i);
+      const float2 fs = *reinterpret_cast<const float2*>(ss + i);
+      const float2 fu = up ? *reinterpret_cast<const float2*>(su + i) : make_float2(0.f, 0.f);
+      const float2 fd = dn ? *reinterpret_cast<const float2*>(sd + i) : make_float2(0.f, 0.f);
+      const float4 o = resupd_pair(f, sc[wrap_prev(i, nx)], sc[wrap_add(i, 2, nx)], fn, fs, fu, fd, up, dn, ro[q],
+                                   ca, cc, cd, xh, xl, yh, yl);
+      if (stats) rr = fmaf(o.x, o.x, fmaf(o.z, o.z, rr));
+      val[q] = make_float2(o.x, o.z);
+      reinterpret_cast<float4*>(rres + r0 + i)[0] = o;
+    }
+    __syncthreads();  // the transform buffers lie over the staged rows
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[pad8(t + q * T)] = val[q];
+  } else if (active) {
     const int nx = g.nx;
     k = row / g.ny;
     const size_t r0 = (size_t)row * nx;
@@ -392,34 +504,13 @@ __global__ void __launch_bounds__(512) k_r2c_x32(Grid g, Metric m, const double*
         const float fe = dprev[r0 + (wrap_add(i, 2, nx))];
         const float2 fn = *reinterpret_cast<const float2*>(dprev + rjp + i);
         const float2 fs = *reinterpret_cast<const float2*>(dprev + rjm + i);
-        // S = L delta = rdx2 (w + e) + rdy2 (s + n) + pc up + pa down - pdiag centre
-        float sxh = 0.f, sxl = 0.f, syh = 0.f, syl = 0.f;
-        ff_acc(sxh, sxl, -cd.x, -cd.y, f.x);
-        ff_acc(syh, syl, -cd.x, -cd.y, f.y);
-        ff_acc(sxh, sxl, xh, xl, fw);
-        ff_acc(sxh, sxl, xh, xl, f.y);
-        ff_acc(syh, syl, xh, xl, f.x);
-        ff_acc(syh, syl, xh, xl, fe);
-        ff_acc(sxh, sxl, yh, yl, fn.x);
-        ff_acc(sxh, sxl, yh, yl, fs.x);
-        ff_acc(syh, syl, yh, yl, fn.y);
-        ff_acc(syh, syl, yh, yl, fs.y);
-        if (up) {
-          const float2 fu = *reinterpret_cast<const float2*>(dprev + r0 + NXY + i);
-          ff_acc(sxh, sxl, cc.x, cc.y, fu.x);
-          ff_acc(syh, syl, cc.x, cc.y, fu.y);
-        }
-        if (dn) {
-          const float2 fd = *reinterpret_cast<const float2*>(dprev + r0 - NXY + i);
-          ff_acc(sxh, sxl, ca.x, ca.y, fd.x);
-          ff_acc(syh, syl, ca.x, ca.y, fd.y);
-        }
+        const float2 fu = up ? *reinterpret_cast<const float2*>(dprev + r0 + NXY + i) : make_float2(0.f, 0.f);
+        const float2 fd = dn ? *reinterpret_cast<const float2*>(dprev + r0 - NXY + i) : make_float2(0.f, 0.f);
         const float4 ro = reinterpret_cast<const float4*>(rres + r0 + i)[0];
-        const float2 nx2 = ff_sub(ro.x, ro.y, sxh, sxl);
-        const float2 ny2 = ff_sub(ro.z, ro.w, syh, syl);
-        if (stats) rr = fmaf(nx2.x, nx2.x, fmaf(ny2.x, ny2.x, rr));
-        buf[pad8(n)] = make_float2(nx2.x, ny2.x);
-        reinterpret_cast<float4*>(rres + r0 + i)[0] = make_float4(nx2.x, nx2.y, ny2.x, ny2.y);
+        const float4 o = resupd_pair(f, fw, fe, fn, fs, fu, fd, up, dn, ro, ca, cc, cd, xh, xl, yh, yl);
+        if (stats) rr = fmaf(o.x, o.x, fmaf(o.z, o.z, rr));
+        buf[pad8(n)] = make_float2(o.x, o.z);
+        reinterpret_cast<float4*>(rres + r0 + i)[0] = o;
       }
     }
   }
@@ -1430,13 +1521,20 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_
   {
     ProfScope ps(c, KF_R2C);
     const int T = g.M / 8, lines = r2c_lines<float>(g);
-    const size_t sm = (size_t)lines * line_smem<float>(g.M) + (size_t)g.nx * sizeof(float2);
+    // the update stages its stencil rows when every block lies in one plane
+    const int mode = it == 0 ? R32_FIRST
+                             : (it == 1 ? R32_RESID : (g.ny % lines == 0 && T <= 256 ? R32_RESUPD_ST : R32_RESUPD));
+    const size_t sm = (size_t)r2c32_front_words(mode, lines, g.nx, pad8(g.M) + 1) * sizeof(float2) +
+                      (size_t)g.nx * sizeof(float2);
     const int blocks = ceil_div((long long)g.nz * g.ny, lines);
     const bool gen = !is_pow2(g.M);
-    auto kf = gen ? (it == 0 ? k_r2c_x32<R32_FIRST, true>
-                             : (it == 1 ? k_r2c_x32<R32_RESID, true> : k_r2c_x32<R32_RESUPD, true>))
-                  : (it == 0 ? k_r2c_x32<R32_FIRST, false>
-                             : (it == 1 ? k_r2c_x32<R32_RESID, false> : k_r2c_x32<R32_RESUPD, false>));
+    auto pick = [&](auto k0, auto k1, auto k2, auto k3) {
+      return mode == R32_FIRST ? k0 : (mode == R32_RESID ? k1 : (mode == R32_RESUPD ? k2 : k3));
+    };
+    auto kf = gen ? pick(k_r2c_x32<R32_FIRST, true>, k_r2c_x32<R32_RESID, true>, k_r2c_x32<R32_RESUPD, true>,
+                         k_r2c_x32<R32_RESUPD_ST, true>)
+                  : pick(k_r2c_x32<R32_FIRST, false>, k_r2c_x32<R32_RESID, false>, k_r2c_x32<R32_RESUPD, false>,
+                         k_r2c_x32<R32_RESUPD_ST, false>);
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, b, phi_in, spec, c->twx32, c->scal, c->part3,
                                              stats ? 1 : 0, skip, c->rres, c->dprev, c->cff);
