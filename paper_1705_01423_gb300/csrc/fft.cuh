@@ -144,8 +144,15 @@ template <int TK> struct ColIx {
 // line (8 | N); it takes butterflies j = t + b N/8 < N/R, b < ceil(8/R). All
 // reads happen before the barrier, all writes after it, so the pass is in
 // place. The caller guarantees that every thread of the block calls this
-// (barriers inside).
-template <int R, bool INV, typename C, typename IX>
+// (barriers inside). PT: `tw` is this pass's own table, entry (r - 1) p + k =
+// w^(r k N/(p R)) (see pass_twiddles), so that lanes with consecutive k read
+// consecutive entries. XM (R = 8, first pass only): butterfly j writes its
+// outputs in the order r ^ (j & XM) instead of r, the same values to the same
+// slots: in a tile of TK-wide rows (ColIx<TK>) the lanes of a warp hold 32 / TK
+// consecutive j, whose outputs 8 j + r lie 8 rows apart, all in the same banks
+// when the rows are 32 or 64 bytes wide; rotating r spreads each store over
+// the 128 bytes of banks (XM = 3 for TK = 4, 1 for TK = 8).
+template <int R, bool INV, typename C, typename IX, bool PT = false, int XM = 0>
 __device__ __forceinline__ void stockham_pass_ix(C* buf, int N, int p, const C* tw, int twstride,
                                                  int t, bool active, IX ix) {
   constexpr int B = (8 + R - 1) / R;  // butterflies per thread (at most)
@@ -174,7 +181,7 @@ __device__ __forceinline__ void stockham_pass_ix(C* buf, int N, int p, const C* 
           const int step = (N / (p * R)) * twstride;
 #pragma unroll
           for (int r = 1; r < R; ++r) {
-            const C w = tw[r * k * step];
+            const C w = PT ? tw[(r - 1) * p + k] : tw[r * k * step];
             y[r] = INV ? cmulc(y[r], w) : cmul(y[r], w);
           }
         }
@@ -184,8 +191,29 @@ __device__ __forceinline__ void stockham_pass_ix(C* buf, int N, int p, const C* 
         if (R == 3) dft3<INV>(y[0], y[1], y[2]);
         if (R == 5) dft5<INV>(y);
         const int o = (j - k) * R + k;
+        if constexpr (XM != 0 && R == 8) {
+          const int sx = j & XM;  // y[r] <- y[r ^ sx], then slot r ^ sx gets y[r]
+          auto swp = [](C& a, C& b2) {
+            const C tmp = a;
+            a = b2;
+            b2 = tmp;
+          };
+          if (sx & 1) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[ix(o + r * p)] = y[r];
+            for (int r = 0; r < 8; r += 2) swp(y[r], y[r + 1]);
+          }
+          if ((XM & 2) && (sx & 2)) {
+            swp(y[0], y[2]);
+            swp(y[1], y[3]);
+            swp(y[4], y[6]);
+            swp(y[5], y[7]);
+          }
+#pragma unroll
+          for (int r = 0; r < 8; ++r) buf[ix(o + (r ^ sx) * p)] = y[r];
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) buf[ix(o + r * p)] = y[r];
+        }
       }
     }
   }
@@ -234,6 +262,47 @@ __device__ __forceinline__ void fft_line_ix(C* buf, int N, const C* tw, int twst
       rest /= 5;
     }
   }
+}
+
+// Per-pass twiddle tables of a power-of-two transform of length N (8 | N), in
+// pass order, for the passes with span p > 1: R - 1 rows of p entries each,
+// entry (r - 1) p + k = tw[r k N/(p R)] (tw: the table of length N). The rows
+// add up to N - 1 entries (each pass's (R - 1) p is the next span minus this
+// one). Filled by the threads of the block (tid of nthr); the caller
+// synchronises before use.
+template <typename C>
+__device__ __forceinline__ void pass_twiddles(C* out, const C* __restrict__ tw, int N, int tid, int nthr) {
+  int off = 0, p = 1, n2 = N;
+  while (n2 > 1) {
+    const int R = n2 >= 8 ? 8 : n2;
+    if (p > 1) {
+      const int step = N / (p * R), n = (R - 1) * p;
+      for (int i = tid; i < n; i += nthr) {
+        const int r = i / p + 1, k = i - (r - 1) * p;
+        out[off + i] = tw[r * k * step];
+      }
+      off += n;
+    }
+    p *= R;
+    n2 /= R;
+  }
+}
+
+// fft_line_ix for a power-of-two N with the per-pass twiddle tables of
+// pass_twiddles in `tabs`: the same arithmetic, the same results.
+// XM: see stockham_pass_ix (the first pass).
+template <bool INV, int XM, typename C, typename IX>
+__device__ __forceinline__ void fft_line_pt_ix(C* buf, int N, const C* tabs, int t, bool active, IX ix) {
+  stockham_pass_ix<8, INV, C, IX, true, XM>(buf, N, 1, tabs, 1, t, active, ix);
+  int p = 8, n2 = N / 8, off = 0;
+  while (n2 >= 8) {
+    stockham_pass_ix<8, INV, C, IX, true>(buf, N, p, tabs + off, 1, t, active, ix);
+    if (p > 1) off += 7 * p;
+    p *= 8;
+    n2 /= 8;
+  }
+  if (n2 == 4) stockham_pass_ix<4, INV, C, IX, true>(buf, N, p, tabs + off, 1, t, active, ix);
+  else if (n2 == 2) stockham_pass_ix<2, INV, C, IX, true>(buf, N, p, tabs + off, 1, t, active, ix);
 }
 
 template <bool INV, bool GEN, typename C>

@@ -64,7 +64,10 @@ __global__ void __launch_bounds__(kTmaMaxThreads, 1) k_fft_y_tma(const __grid_co
     for (int s = 0; s < stages; ++s) mbar_init(&bar[s], 1);
     fence_barrier_init();
   }
-  for (int q = tid; q < N; q += blockDim.x) stw[q] = tw[q];
+  // per-pass twiddle tables (N - 1 entries): the lanes of a warp hold 32 / TK
+  // consecutive butterflies, whose twiddles in the table of length N lie
+  // r k N/(p R) apart (up to 8-way bank conflicts at TK = 4)
+  pass_twiddles(stw, tw, N, tid, blockDim.x);
   __syncthreads();
 
   // thread 0: start the loads of local tile `it` into stage it % stages. The
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(kTmaMaxThreads, 1) k_fft_y_tma(const __grid_co
       break;
     }
     C* buf = tiles + (size_t)s * tile_elems;
-    fft_line_ix<INV, false>(buf, N, stw, 1, t, true, ColIx<TK>{c});
+    fft_line_pt_ix<INV, TK == 4 ? 3 : (TK == 8 ? 1 : 0)>(buf, N, stw, t, true, ColIx<TK>{c});
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
