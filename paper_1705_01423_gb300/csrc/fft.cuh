@@ -266,12 +266,13 @@ __device__ __forceinline__ void fft_line_ix(C* buf, int N, const C* tw, int twst
 
 // Per-pass twiddle tables of a power-of-two transform of length N (8 | N), in
 // pass order, for the passes with span p > 1: R - 1 rows of p entries each,
-// entry (r - 1) p + k = tw[r k N/(p R)] (tw: the table of length N). The rows
-// add up to N - 1 entries (each pass's (R - 1) p is the next span minus this
-// one). Filled by the threads of the block (tid of nthr); the caller
-// synchronises before use.
+// entry (r - 1) p + k = tw[r k N/(p R) twstride] (tw read with the stride of
+// its length over N). The rows add up to N - 8 entries (each pass's (R - 1) p
+// is the next span minus this one). Filled by the threads of the block (tid
+// of nthr); the caller synchronises before use.
 template <typename C>
-__device__ __forceinline__ void pass_twiddles(C* out, const C* __restrict__ tw, int N, int tid, int nthr) {
+__device__ __forceinline__ void pass_twiddles(C* out, const C* __restrict__ tw, int N, int twstride, int tid,
+                                              int nthr) {
   int off = 0, p = 1, n2 = N;
   while (n2 > 1) {
     const int R = n2 >= 8 ? 8 : n2;
@@ -279,7 +280,7 @@ __device__ __forceinline__ void pass_twiddles(C* out, const C* __restrict__ tw, 
       const int step = N / (p * R), n = (R - 1) * p;
       for (int i = tid; i < n; i += nthr) {
         const int r = i / p + 1, k = i - (r - 1) * p;
-        out[off + i] = tw[r * k * step];
+        out[off + i] = tw[r * k * step * twstride];
       }
       off += n;
     }
@@ -305,6 +306,11 @@ __device__ __forceinline__ void fft_line_pt_ix(C* buf, int N, const C* tabs, int
   else if (n2 == 2) stockham_pass_ix<2, INV, C, IX, true>(buf, N, p, tabs + off, 1, t, active, ix);
 }
 
+template <bool INV, typename C>
+__device__ __forceinline__ void fft_line_pt(C* buf, int N, const C* tabs, int t, bool active) {
+  fft_line_pt_ix<INV, 0>(buf, N, tabs, t, active, PadIx{});
+}
+
 template <bool INV, bool GEN, typename C>
 __device__ __forceinline__ void fft_line(C* buf, int N, const C* tw, int twstride, int t, bool active) {
   fft_line_ix<INV, GEN>(buf, N, tw, twstride, t, active, PadIx{});
@@ -316,9 +322,11 @@ __device__ __forceinline__ void fft_line(C* buf, int N, const C* tw, int twstrid
 // its outputs to the padded line, saving one shared-memory round trip; the
 // remaining passes follow as in fft_line. The arithmetic is that of
 // fft_line, in the same order. Every thread of the block calls it (barriers).
-template <bool INV, bool GEN, typename C>
+// PT (power-of-two N only): `tw` holds the per-pass tables of pass_twiddles.
+template <bool INV, bool GEN, bool PT = false, typename C>
 __device__ __forceinline__ void fft_line_from_regs(C* buf, int N, C* x, const C* tw, int twstride, int t,
                                                    bool active) {
+  static_assert(!(PT && GEN), "per-pass tables cover power-of-two lengths");
   if (active) {
     dft8<INV>(x);
 #pragma unroll
@@ -328,16 +336,18 @@ __device__ __forceinline__ void fft_line_from_regs(C* buf, int N, C* x, const C*
   int p = 8;
   int n2 = (N & -N) / 8;
   int rest = N / (N & -N);
+  int off = 0;  // PT: offset of the pass's table
   while (n2 >= 8) {
-    stockham_pass<8, INV>(buf, N, p, tw, twstride, t, active);
+    stockham_pass_ix<8, INV, C, PadIx, PT>(buf, N, p, tw + off, twstride, t, active, PadIx{});
+    if (PT) off += 7 * p;
     p *= 8;
     n2 /= 8;
   }
   if (n2 == 4) {
-    stockham_pass<4, INV>(buf, N, p, tw, twstride, t, active);
+    stockham_pass_ix<4, INV, C, PadIx, PT>(buf, N, p, tw + off, twstride, t, active, PadIx{});
     p *= 4;
   } else if (n2 == 2) {
-    stockham_pass<2, INV>(buf, N, p, tw, twstride, t, active);
+    stockham_pass_ix<2, INV, C, PadIx, PT>(buf, N, p, tw + off, twstride, t, active, PadIx{});
     p *= 2;
   }
   if constexpr (GEN) {
@@ -361,7 +371,8 @@ __device__ __forceinline__ void fft_line_from_regs(C* buf, int N, C* x, const C*
 // and writes point j + r p, i.e. q = b + r 8/R. The line in shared memory is
 // left as the previous pass wrote it. The arithmetic is that of fft_line, in
 // the same order. Every thread of the block calls it (barriers).
-template <bool INV, typename C>
+// PT: `tw` holds the per-pass tables of pass_twiddles.
+template <bool INV, bool PT = false, typename C>
 __device__ __forceinline__ void fft_line_pow2_to_regs(C* buf, int N, C* out, const C* tw, int twstride,
                                                       int t, bool active) {
   int passes8 = 0, n2 = N;
@@ -371,9 +382,10 @@ __device__ __forceinline__ void fft_line_pow2_to_regs(C* buf, int N, C* out, con
   }
   const int last = n2 == 4 ? 4 : (n2 == 2 ? 2 : 8);  // radix of the last pass
   if (last == 8) --passes8;
-  int p = 1;
+  int p = 1, off = 0;
   for (int i = 0; i < passes8; ++i) {
-    stockham_pass<8, INV>(buf, N, p, tw, twstride, t, active);
+    stockham_pass_ix<8, INV, C, PadIx, PT>(buf, N, p, tw + off, twstride, t, active, PadIx{});
+    if (PT && p > 1) off += 7 * p;
     p *= 8;
   }
   if (!active) return;
@@ -396,7 +408,7 @@ __device__ __forceinline__ void fft_line_pow2_to_regs(C* buf, int N, C* out, con
       if (p > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const C w = tw[r * k * twstride];
+          const C w = PT ? tw[off + (r - 1) * p + k] : tw[r * k * twstride];
           y[r] = INV ? cmulc(y[r], w) : cmul(y[r], w);
         }
       }

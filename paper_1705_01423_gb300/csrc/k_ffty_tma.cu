@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kTmaMaxThreads, 1) k_fft_y_tma(const __grid_co
   // per-pass twiddle tables (N - 1 entries): the lanes of a warp hold 32 / TK
   // consecutive butterflies, whose twiddles in the table of length N lie
   // r k N/(p R) apart (up to 8-way bank conflicts at TK = 4)
-  pass_twiddles(stw, tw, N, tid, blockDim.x);
+  pass_twiddles(stw, tw, N, 1, tid, blockDim.x);
   __syncthreads();
 
   // thread 0: start the loads of local tile `it` into stage it % stages. The

@@ -177,7 +177,9 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
   const int stride = pad8(M) + 1;
   C* buf = sm + line * stride;
   C* stw = sm + lines * stride;  // twiddle table, nx entries
+  C* stp = stw + g.nx;           // per-pass tables of the M-point FFT (power-of-two M)
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
+  if (!GEN) pass_twiddles(stp, tw, M, 2, threadIdx.x, blockDim.x);
   double amax = 0.0;
   if (active) {
     const int nx = g.nx;
@@ -218,7 +220,8 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
     }
   }
   __syncthreads();
-  fft_line<false, GEN>(buf, M, stw, 2, t, active);
+  if constexpr (GEN) fft_line<false, true>(buf, M, stw, 2, t, active);
+  else fft_line_pt<false>(buf, M, stp, t, active);
   if (active) {
     C* out = spec + (size_t)row * g.P;
     const R half = (R)0.5;
@@ -339,7 +342,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 }
 
 template <int MODE, bool GEN>
-__global__ void __launch_bounds__(MODE == R32_RESUPD_ST ? 256 : 512, MODE == R32_RESUPD_ST ? 3 : 1) k_r2c_x32(Grid g, Metric m, const double* __restrict__ b,
+__global__ void __launch_bounds__(MODE == R32_RESUPD_ST ? 256 : 512, MODE == R32_RESUPD_ST ? 3 : 0) k_r2c_x32(Grid g, Metric m, const double* __restrict__ b,
                                                  const double* __restrict__ phi, float2* __restrict__ spec,
                                                  const float2* __restrict__ tw, double* __restrict__ scal,
                                                  double* __restrict__ part, int stats,
@@ -359,7 +362,9 @@ __global__ void __launch_bounds__(MODE == R32_RESUPD_ST ? 256 : 512, MODE == R32
   const int stride = pad8(M) + 1;
   float2* buf = sm + line * stride;
   float2* stw = sm + r2c32_front_words(MODE, lines, g.nx, stride);  // twiddle table, nx entries
+  float2* stp = stw + g.nx;  // per-pass tables of the M-point FFT (power-of-two M)
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
+  if (!GEN) pass_twiddles(stp, tw, M, 2, threadIdx.x, blockDim.x);
   float fs = 0.f, fc = 0.f, fs2 = 0.f;  // FIRST: compensated FP32 row sum, sum of squares
   float2 zr[8];                         // FIRST: the thread's points, for the first FFT pass
   float rr = 0.f;
@@ -515,10 +520,12 @@ __global__ void __launch_bounds__(MODE == R32_RESUPD_ST ? 256 : 512, MODE == R32
     }
   }
   if (MODE == R32_FIRST) {
-    fft_line_from_regs<false, GEN>(buf, M, zr, stw, 2, t, active);
+    if constexpr (GEN) fft_line_from_regs<false, true>(buf, M, zr, stw, 2, t, active);
+    else fft_line_from_regs<false, false, true>(buf, M, zr, stp, 2, t, active);
   } else {
     __syncthreads();
-    fft_line<false, GEN>(buf, M, stw, 2, t, active);
+    if constexpr (GEN) fft_line<false, true>(buf, M, stw, 2, t, active);
+    else fft_line_pt<false>(buf, M, stp, t, active);
   }
   if (active) {
     float2* out = spec + (size_t)row * g.P;
@@ -592,7 +599,9 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
   const int stride = pad8(M) + 1;
   C* buf = sm + line * stride;
   C* stw = sm + lines * stride;  // twiddle table, nx entries
+  C* stp = stw + g.nx;           // per-pass tables of the M-point FFT (power-of-two M)
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
+  if (!GEN) pass_twiddles(stp, tw, M, 2, threadIdx.x, blockDim.x);
   if (active) {
     const C* in = spec + (size_t)row * g.P;
     for (int k = t; k <= M; k += T) buf[pad8(k)] = in[k];
@@ -618,8 +627,9 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
   // its outputs are the thread's points t + q T written out below
   constexpr bool REGS = !GEN && std::is_same<R, float>::value;
   C zr[8];
-  if (REGS) fft_line_pow2_to_regs<true>(buf, M, zr, stw, 2, t, active);
-  else fft_line<true, GEN>(buf, M, stw, 2, t, active);
+  if constexpr (REGS) fft_line_pow2_to_regs<true, true>(buf, M, zr, stp, 2, t, active);
+  else if constexpr (GEN) fft_line<true, true>(buf, M, stw, 2, t, active);
+  else fft_line_pt<true>(buf, M, stp, t, active);
   R d2 = (R)0, dsum = (R)0, dcomp = (R)0;
   double psum = 0.0;
   if (active) {
@@ -1432,7 +1442,7 @@ static cudaError_t run_r2c(afid_ctx* c, const double* rhs, const double* u, cons
   ProfScope ps(c, KF_R2C);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
-  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)g.nx * sizeof(typename cplx<R>::T);
+  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + g.M) * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   const bool gen = !is_pow2(g.M);
   if (rhs) {
@@ -1457,7 +1467,7 @@ static cudaError_t run_c2r(afid_ctx* c, const typename cplx<R>::T* spec,
   ProfScope ps(c, KF_C2R);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
-  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)g.nx * sizeof(typename cplx<R>::T);
+  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + g.M) * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   const double scale = 1.0 / ((double)g.nx * (double)g.ny);
   const bool gen = !is_pow2(g.M);
@@ -1525,7 +1535,7 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_
     const int mode = it == 0 ? R32_FIRST
                              : (it == 1 ? R32_RESID : (g.ny % lines == 0 && T <= 256 ? R32_RESUPD_ST : R32_RESUPD));
     const size_t sm = (size_t)r2c32_front_words(mode, lines, g.nx, pad8(g.M) + 1) * sizeof(float2) +
-                      (size_t)g.nx * sizeof(float2);
+                      (size_t)(g.nx + g.M) * sizeof(float2);
     const int blocks = ceil_div((long long)g.nz * g.ny, lines);
     const bool gen = !is_pow2(g.M);
     auto pick = [&](auto k0, auto k1, auto k2, auto k3) {
