@@ -167,7 +167,7 @@ def family_work(fam: str, w):
       c2r_x  packing 4 + fft_ops(nx/2)/2 + scaling 1
       fft_y  fft_ops(ny) per complex point (nx/2+1 complex per row)
       thomas 7 per complex point (4 forward, 3 backward)
-      project 9; rhs 108 (shared face fluxes 29, u 19, v 19, w 21, T 17, per-plane
+      project 9; rhs 104 (shared face fluxes 29, u 18, v 18, w 20, T 16, per-plane
       factors 3; the recomputed fluxes of the warp- and block-edge neighbours are
       overhead, not counted); crank_nicolson 8 (4 fields: one forward-elimination
       FMA, the reciprocal pivot being folded into the right-hand side the
@@ -189,7 +189,7 @@ def family_work(fam: str, w):
     if fam == "project":
         return 72 * n, 9 * n
     if fam == "rhs":
-        return 136 * n, 108 * n
+        return 136 * n, 104 * n
     if fam == "crank_nicolson":
         return 4 * 24 * n, 8 * n
     if fam == "cfl_reduce":
@@ -991,13 +991,14 @@ def multires_measurement(ctx, w, dev, r=(2, 2, 2), n_sub=1, reps=3, fp64_peak=FP
     fine = m.nx * m.ny * m.nz
     nsubst = 3 * n_sub  # refined substeps per coupled step
     # FP64 operation model per fine point and substep: the temperature terms
-    # with shared face fluxes (31: own x and y face fluxes 8, the block-edge
+    # with shared face fluxes (30: own x and y face fluxes 8, the block-edge
     # fluxes 2 + 1 (64-wide rows, 4 rows), z flux 3, divergence 6, horizontal
-    # Laplacian 5, H 1, CN explicit side 3, R 2) and the prolongation (per
+    # diffusion with kappa folded into its weights, forming H, 5, CN explicit
+    # side 3, R 2) and the prolongation (per
     # component a z interpolation, 2, plus per coarse plane a y interpolation,
     # 2, and the column's share of the block's x interpolations of 8/ry + 1
     # coarse rows, 2 (8/ry + 1) / 8, shared by rz fine levels)
-    ops_rhs = 31.0 * fine * nsubst
+    ops_rhs = 30.0 * fine * nsubst
     ops_pro = 3 * (2.0 + (2.0 + 2.0 * (8.0 / r[1] + 1.0) / 8.0) / r[2]) * fine * nsubst
     peak = fp64_peak * 1e12
     out = {"refinement": list(r), "n_sub": n_sub, "fine_grid": [m.nx, m.ny, m.nz],

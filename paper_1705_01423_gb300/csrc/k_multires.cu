@@ -227,7 +227,15 @@ __global__ void k_mr_restrict(Grid gc, Grid gf, int rx, int ry, int rz, const do
 //   R = dt [gamma_l H + rho_l Hprev] + alpha_l dt kappa dzz T.
 // One thread per (x, y) column, walking up in k and carrying the z flux, the
 // lower-plane velocities and the three T values of the column.
-__global__ void __launch_bounds__(256) k_mr_scalar_rhs(Grid g, Metric m, double kappa, int l, double dt,
+// Scalar factors of the temperature terms, formed on the host (as kernel
+// parameters they sit in the constant bank, read directly by the FMAs): 1/2 of
+// the inverse spacings and the horizontal diffusion weights with kappa folded
+// in, kappa/dx^2, kappa/dy^2, 2 kappa (1/dx^2 + 1/dy^2).
+struct ScalarW {
+  double hx, hy, krx, kry, kl0;
+};
+
+__global__ void __launch_bounds__(256) k_mr_scalar_rhs(Grid g, Metric m, ScalarW sw, int l, double dt,
                                                        const double* __restrict__ u,
                                                        const double* __restrict__ v,
                                                        const double* __restrict__ w,
@@ -250,8 +258,7 @@ __global__ void __launch_bounds__(256) k_mr_scalar_rhs(Grid g, Metric m, double 
   const double* __restrict__ mcg = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MCG) * L;
   const double* __restrict__ mcr = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MCR) * L;
   (void)dt;
-  const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
-  const double lap0 = 2.0 * (g.rdx2 + g.rdy2);
+  const double hx = sw.hx, hy = sw.hy;
   const double* __restrict__ ea = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MEA) * L;  // m alpha dt kappa dzz
   const double* __restrict__ ec = ea + L;
   const double* __restrict__ ed = ec + L;
@@ -282,8 +289,7 @@ __global__ void __launch_bounds__(256) k_mr_scalar_rhs(Grid g, Metric m, double 
     const double fy0 = vfj * (tjm + t0), fy1 = vfjp * (t0 + tjp);
     const double fz1 = (w0 + wk1) * (t0 + tk1);
     const double A = fma(fz1 - fz0, qzf[k], fma(fy1 - fy0, hy, (fx1 - fx0) * hx));
-    const double lap = fma(-lap0, t0, fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2));
-    const double H = fma(kappa, lap, -A);
+    const double H = fma(sw.krx, tip + tim, fma(sw.kry, tjp + tjm, fma(-sw.kl0, t0, -A)));
     const double z = fma(ea[k], tkm, fma(ec[k], tk1, ed[k] * t0));
     double r = fma(mcg[k], H, z);
     if (l > 0) r = fma(mcr[k], HT[c + col], r);
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(256) k_mr_scalar_rhs(Grid g, Metric m, double 
 // branch costs its warp the full instruction count: wider blocks have fewer.
 template <int BY, int WPR>
 __global__ void __launch_bounds__(32 * WPR * BY, 2) k_mr_scalar_rhs_sh(
-    Grid g, Metric m, double kappa, int l, double dt, const double* __restrict__ u,
+    Grid g, Metric m, ScalarW sw, int l, double dt, const double* __restrict__ u,
     const double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ T,
     double* __restrict__ HT, double* __restrict__ RT, const double* __restrict__ cnt, int kchunk) {
   constexpr int BX = 32 * WPR;
@@ -331,8 +337,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_mr_scalar_rhs_sh(
   const double* __restrict__ mcg = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MCG) * L;
   const double* __restrict__ mcr = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MCR) * L;
   (void)dt;
-  const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
-  const double lap0 = 2.0 * (g.rdx2 + g.rdy2);
+  const double hx = sw.hx, hy = sw.hy;
   const double* __restrict__ ea = cnt + (size_t)(2 * CN_TAB_ARRAYS + CN_MEA) * L;
   const double* __restrict__ ec = ea + L;
   const double* __restrict__ ed = ec + L;
@@ -377,8 +382,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, 2) k_mr_scalar_rhs_sh(
       fyt = sfy[buf][ty + 1][tx];
     const double fz1 = (w0 + wk1) * (t0 + tk1);
     const double A = fma(fz1 - fz0, qzf[k], fma(fyt - fyb, hy, (fxr - fxl) * hx));
-    const double lap = fma(-lap0, t0, fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2));
-    const double H = fma(kappa, lap, -A);
+    const double H = fma(sw.krx, tip + tim, fma(sw.kry, tjp + tjm, fma(-sw.kl0, t0, -A)));
     const double z = fma(ea[k], tkm, fma(ec[k], tk1, ed[k] * t0));
     double r = fma(mcg[k], H, z);
     if (l > 0) r = fma(mcr[k], HT[c + col], r);
@@ -484,14 +488,16 @@ cudaError_t scalar_substep(afid_mr* mr, int l, double dts, double* Tf) {
     const long long bpp = (long long)ceil_div(gf.nx, bx) * ceil_div(gf.ny, by);
     const int kc = z_chunk(c, bpp, gf.nz);
     dim3 grd(ceil_div(gf.nx, bx), ceil_div(gf.ny, by), ceil_div(gf.nz, kc));
+    const double ka = c->phys.kappa;
+    const ScalarW sw{0.5 * gf.rdx, 0.5 * gf.rdy, ka * gf.rdx2, ka * gf.rdy2, 2.0 * (ka * gf.rdx2 + ka * gf.rdy2)};
     if (shared && wpr == 2)
-      k_mr_scalar_rhs_sh<4, 2><<<grd, blk, 0, c->stream>>>(gf, mr->mf, c->phys.kappa, l, dts, mr->uf, mr->vf,
+      k_mr_scalar_rhs_sh<4, 2><<<grd, blk, 0, c->stream>>>(gf, mr->mf, sw, l, dts, mr->uf, mr->vf,
                                                            mr->wf, Tf, mr->HT, mr->RT, mr->cntab, kc);
     else if (shared)
-      k_mr_scalar_rhs_sh<8, 1><<<grd, blk, 0, c->stream>>>(gf, mr->mf, c->phys.kappa, l, dts, mr->uf, mr->vf,
+      k_mr_scalar_rhs_sh<8, 1><<<grd, blk, 0, c->stream>>>(gf, mr->mf, sw, l, dts, mr->uf, mr->vf,
                                                            mr->wf, Tf, mr->HT, mr->RT, mr->cntab, kc);
     else
-      k_mr_scalar_rhs<<<grd, blk, 0, c->stream>>>(gf, mr->mf, c->phys.kappa, l, dts, mr->uf, mr->vf, mr->wf,
+      k_mr_scalar_rhs<<<grd, blk, 0, c->stream>>>(gf, mr->mf, sw, l, dts, mr->uf, mr->vf, mr->wf,
                                                   Tf, mr->HT, mr->RT, mr->cntab, kc);
     c->launches++;
   }

@@ -30,8 +30,15 @@
 
 namespace afid {
 
+// Scalar factors of the kernel, formed on the host: as kernel parameters they
+// sit in the constant bank, where an FMA reads them directly (computed in the
+// kernel they would hold registers or be recomputed in the loop).
 struct PhysR {
-  double nu, kappa, buoy, ubot, utop;
+  double buoy, ubot, utop;
+  double qx, qy;          // 1/4 of the inverse spacings
+  double hx, hy;          // 1/2 of the inverse spacings
+  double nrx, nry, nl0;   // nu / dx^2, nu / dy^2, 2 nu (1/dx^2 + 1/dy^2)
+  double krx, kry, kl0;   // the same with kappa
 };
 
 // WPR warps per block row: 1 (BX = min(32, nx), BY = 8; two blocks per SM) or
@@ -78,9 +85,11 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
   const int L = nz + 1;
   // this block's range of k (the z-march is split into chunks for load balance)
   const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
-  const double qx = 0.25 * g.rdx, qy = 0.25 * g.rdy;  // 1/4 of the inverse spacings
-  const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
-  const double lap0 = 2.0 * (g.rdx2 + g.rdy2);
+  // horizontal diffusion nu (d_xx + d_yy) q as nu rdx2 (q_i+1 + q_i-1) +
+  // nu rdy2 (q_j+1 + q_j-1) - 2 nu (rdx2 + rdy2) q: the diffusivity folded
+  // into the three weights (kappa for T)
+  const double qx = ph.qx, qy = ph.qy, hx = ph.hx, hy = ph.hy;
+  const double nrx = ph.nrx, nry = ph.nry, nl0 = ph.nl0, krx = ph.krx, kry = ph.kry, kl0 = ph.kl0;
 
   // shared y-exchange: [buffer][quantity][row][x]; x-edge exchange between
   // the two warps of a row: fxw, fxt of x = 32 and fxu of x = 31
@@ -229,8 +238,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
     const double qz = cnt[CN_QZ * L + k];  // dzc^-1 / 4
     {
       const double A = fma(fzu1 - fzu, qz, fma(Cjp - C, qy, (fxu - fxum) * qx));
-      const double lap = fma(-lap0, u0, fma(ujp + ujm, g.rdy2, (uip + uim) * g.rdx2));
-      const double H = fma(ph.nu, lap, -A);
+      const double H = fma(nrx, uip + uim, fma(nry, ujp + ujm, fma(-nl0, u0, -A)));
       const double z = fma(cnt[CN_MEA * L + k], ukm, fma(cnt[CN_MEC * L + k], ukp, fma(cnt[CN_MED * L + k], u0, -cnt[CN_MGX * L + k] * (p0 - p[c + cim]))));
       double r = fma(cnt[CN_MCG * L + k], H, z);
       if (l > 0) r = fma(cnt[CN_MCR * L + k], Hu[c + col], r);
@@ -239,8 +247,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
     }
     {
       const double A = fma(fzv1 - fzv, qz, fma(fyv - fyvm, qy, (Cip - C) * qx));
-      const double lap = fma(-lap0, v0, fma(vjp + vjm, g.rdy2, (vip + vim) * g.rdx2));
-      const double H = fma(ph.nu, lap, -A);
+      const double H = fma(nrx, vip + vim, fma(nry, vjp + vjm, fma(-nl0, v0, -A)));
       const double z = fma(cnt[CN_MEA * L + k], vkm, fma(cnt[CN_MEC * L + k], vkp, fma(cnt[CN_MED * L + k], v0, -cnt[CN_MGY * L + k] * (p0 - p[c + cjm]))));
       double r = fma(cnt[CN_MCG * L + k], H, z);
       if (l > 0) r = fma(cnt[CN_MCR * L + k], Hv[c + col], r);
@@ -259,8 +266,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
       const double qzf = cnt[CN_QZF * L + k];  // dzf^-1 / 4
       {
         const double A = fma(fzw1 - fzw, qzf, fma(fyw1 - fyw, hy, (fxw1 - fxw) * hx));
-        const double lap = fma(-lap0, w0, fma(wjp + wjm0, g.rdy2, (wip + wim0) * g.rdx2));
-        double H = fma(ph.nu, lap, -A);
+        double H = fma(nrx, wip + wim0, fma(nry, wjp + wjm0, fma(-nl0, w0, -A)));
         if (BUOY) H = fma(ph.buoy, t0, H);
         const double z = fma(cnt[(CN_TAB_ARRAYS + CN_MEA) * L + k], wkm, fma(cnt[(CN_TAB_ARRAYS + CN_MEC) * L + k], wk1, fma(cnt[(CN_TAB_ARRAYS + CN_MED) * L + k], w0, -cnt[(CN_TAB_ARRAYS + CN_MGX) * L + k] * (p0 - pkm))));
         double r = fma(cnt[(CN_TAB_ARRAYS + CN_MCG) * L + k], H, z);
@@ -270,8 +276,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
       }
       if (HAS_T) {
         const double A = fma(fzt1 - fzt, qzf, fma(fyt1 - fyt, hy, (fxt1 - fxt) * hx));
-        const double lap = fma(-lap0, t0, fma(tjp + tjm, g.rdy2, (tip + tim) * g.rdx2));
-        const double H = fma(ph.kappa, lap, -A);
+        const double H = fma(krx, tip + tim, fma(kry, tjp + tjm, fma(-kl0, t0, -A)));
         const double z = fma(cnt[(2 * CN_TAB_ARRAYS + CN_MEA) * L + k], tkm, fma(cnt[(2 * CN_TAB_ARRAYS + CN_MEC) * L + k], tk1, cnt[(2 * CN_TAB_ARRAYS + CN_MED) * L + k] * t0));
         double r = fma(cnt[(2 * CN_TAB_ARRAYS + CN_MCG) * L + k], H, z);
         if (l > 0) r = fma(cnt[(2 * CN_TAB_ARRAYS + CN_MCR) * L + k], HT[c + col], r);
@@ -323,7 +328,10 @@ cudaError_t rk3_explicit(afid_ctx* c, int l, double dt, const double* u, const d
   const int kchunk = (g.nz + nch - 1) / nch;
   nch = (g.nz + kchunk - 1) / kchunk;
   dim3 blk(bx, BY), grd(g.nx / bx, g.ny / BY, nch);
-  PhysR ph{c->phys.nu, c->phys.kappa, c->phys.buoyancy, c->phys.u_bot, c->phys.u_top};
+  const double nu = c->phys.nu, ka = c->phys.kappa;
+  PhysR ph{c->phys.buoyancy, c->phys.u_bot, c->phys.u_top, 0.25 * g.rdx, 0.25 * g.rdy, 0.5 * g.rdx, 0.5 * g.rdy,
+           nu * g.rdx2, nu * g.rdy2, 2.0 * (nu * g.rdx2 + nu * g.rdy2),
+           ka * g.rdx2, ka * g.rdy2, 2.0 * (ka * g.rdx2 + ka * g.rdy2)};
 #define AFID_RHS(HT_, BY_, W_)                                                                     \
   k_rhs_zm<HT_, BY_, W_><<<grd, blk, 0, c->stream>>>(g, c->m, ph, l, dt, c->scal, u, v, w, T, p, Hu, Hv, \
                                                      Hw, HT, c->R[0], c->R[1], c->R[2], c->R[3],         \
