@@ -163,8 +163,9 @@ def family_work(fam: str, w):
     (bytes, fp64_ops). Bytes: compulsory HBM traffic of the kernel's own inputs
     and outputs. FP64 operations: the formulation's arithmetic, each add,
     multiply or FMA counted once (per grid point unless noted):
-      r2c_x  divergence 6 + packed real FFT fft_ops(nx/2)/2 + unpacking 4
-      c2r_x  packing 4 + fft_ops(nx/2)/2 + scaling 1
+      r2c_x  divergence 6 + packed real FFT fft_ops(nx/2)/2 + unpacking 3 (its
+             halves folded into FMAs and a halved twiddle table)
+      c2r_x  packing 3 (the 1/(nx ny) normalisation folded in) + fft_ops(nx/2)/2
       fft_y  fft_ops(ny) per complex point (nx/2+1 complex per row)
       thomas 7 per complex point (4 forward, 3 backward)
       project 9; rhs 104 (shared face fluxes 29, u 18, v 18, w 20, T 16, per-plane
@@ -179,9 +180,9 @@ def family_work(fam: str, w):
     M1 = nx // 2 + 1
     nc = M1 * ny * nz
     if fam == "r2c_x":
-        return 24 * n + 16 * nc, (6 + fft_ops(nx // 2) / 2 + 4) * n
+        return 24 * n + 16 * nc, (6 + fft_ops(nx // 2) / 2 + 3) * n
     if fam == "c2r_x":
-        return 16 * nc + 8 * n, (4 + fft_ops(nx // 2) / 2 + 1) * n
+        return 16 * nc + 8 * n, (3 + fft_ops(nx // 2) / 2) * n
     if fam == "fft_y":
         return 32 * nc, fft_ops(ny) * nc
     if fam == "thomas":

@@ -178,8 +178,10 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
   C* buf = sm + line * stride;
   C* stw = sm + lines * stride;  // twiddle table, nx entries
   C* stp = stw + g.nx;           // per-pass tables of the M-point FFT (power-of-two M)
+  C* stq = stp + M;              // unpacking twiddles w_k / 2, k <= M/2
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
   if (!GEN) pass_twiddles(stp, tw, M, 2, threadIdx.x, blockDim.x);
+  for (int q = threadIdx.x; q <= M / 2; q += blockDim.x) stq[q] = cscale(tw[q], (R)0.5);
   double amax = 0.0;
   if (active) {
     const int nx = g.nx;
@@ -233,11 +235,13 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
         continue;
       }
       const C zm = buf[pad8(M - k)];
-      const C E = C{(zk.x + zm.x) * half, (zk.y - zm.y) * half};
-      const C O = C{(zk.y + zm.y) * half, (zm.x - zk.x) * half};
-      const C wO = cmul(O, stw[k]);
-      out[k] = cadd(E, wO);
-      if (k != M / 2) out[M - k] = cconj(csub(E, wO));
+      // X_k = E + w_k O, X_M-k = conj(E - w_k O) with E = (Z_k + conj Z_M-k)/2,
+      // O = (Z_k - conj Z_M-k)/(2i): the halves folded into the FMAs and
+      // into the table (w_k / 2)
+      const C E2 = C{zk.x + zm.x, zk.y - zm.y};
+      const C wO = cmul(C{zk.y + zm.y, zm.x - zk.x}, stq[k]);
+      out[k] = C{fma(half, E2.x, wO.x), fma(half, E2.y, wO.y)};
+      if (k != M / 2) out[M - k] = C{fma(half, E2.x, -wO.x), fma(-half, E2.y, wO.y)};
     }
   }
   if (want_stats) {
@@ -537,6 +541,8 @@ __global__ void __launch_bounds__(MODE == R32_RESUPD_ST ? 256 : 512, MODE == R32
         continue;
       }
       const float2 zm = buf[pad8(M - q)];
+      // FP32 arithmetic is not what limits this kernel: the halves stay as
+      // multiplies (a halved table would cost every block its fill)
       const float2 E = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
       const float2 O = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
       const float2 wO = cmul(O, stw[q]);
@@ -600,8 +606,11 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
   C* buf = sm + line * stride;
   C* stw = sm + lines * stride;  // twiddle table, nx entries
   C* stp = stw + g.nx;           // per-pass tables of the M-point FFT (power-of-two M)
+  C* stq = stp + M;              // MODE 0: packing twiddles scale * w_k, k <= M/2
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
   if (!GEN) pass_twiddles(stp, tw, M, 2, threadIdx.x, blockDim.x);
+  if (MODE == 0)
+    for (int q = threadIdx.x; q <= M / 2; q += blockDim.x) stq[q] = cscale(tw[q], (R)scale);
   if (active) {
     const C* in = spec + (size_t)row * g.P;
     for (int k = t; k <= M; k += T) buf[pad8(k)] = in[k];
@@ -611,15 +620,24 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
     for (int k = t; k <= M / 2; k += T) {
       if (k == 0) {
         const R x0 = buf[pad8(0)].x, xm = buf[pad8(M)].x;
-        buf[pad8(0)] = C{x0 + xm, x0 - xm};
+        buf[pad8(0)] = MODE == 0 ? C{(x0 + xm) * (R)scale, (x0 - xm) * (R)scale} : C{x0 + xm, x0 - xm};
         continue;
       }
       const C a = buf[pad8(k)], b = buf[pad8(M - k)];
       const C E = C{a.x + b.x, a.y - b.y};
-      const C O = cmulc(C{a.x - b.x, a.y + b.y}, stw[k]);
-      // Z'_k = E + i O ; Z'_{M-k} = conj(E) + i conj(O)
-      buf[pad8(k)] = C{E.x - O.y, E.y + O.x};
-      if (k != M / 2) buf[pad8(M - k)] = C{E.x + O.y, O.x - E.y};
+      // Z'_k = E + i O ; Z'_{M-k} = conj(E) + i conj(O). MODE 0 applies the
+      // normalisation here (the transform is linear): O from the scaled
+      // table, E through the FMAs, so the output needs no multiply.
+      if (MODE == 0) {
+        const R sc = (R)scale;
+        const C O = cmulc(C{a.x - b.x, a.y + b.y}, stq[k]);
+        buf[pad8(k)] = C{fma(sc, E.x, -O.y), fma(sc, E.y, O.x)};
+        if (k != M / 2) buf[pad8(M - k)] = C{fma(sc, E.x, O.y), fma(-sc, E.y, O.x)};
+      } else {
+        const C O = cmulc(C{a.x - b.x, a.y + b.y}, stw[k]);
+        buf[pad8(k)] = C{E.x - O.y, E.y + O.x};
+        if (k != M / 2) buf[pad8(M - k)] = C{E.x + O.y, O.x - E.y};
+      }
     }
   }
   __syncthreads();
@@ -643,7 +661,7 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
       const int n = t + q * T;
       const C z = REGS ? zr[q] : buf[pad8(n)];
       if (MODE == 0) {
-        o2[n] = make_double2((double)z.x * scale, (double)z.y * scale);
+        o2[n] = make_double2((double)z.x, (double)z.y);  // normalised in the packing
       } else {
         // rounded products (no contraction into the sums below): the sums
         // must see exactly the values stored in phi
@@ -1442,7 +1460,7 @@ static cudaError_t run_r2c(afid_ctx* c, const double* rhs, const double* u, cons
   ProfScope ps(c, KF_R2C);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
-  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + g.M) * sizeof(typename cplx<R>::T);
+  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + g.M + g.M / 2 + 1) * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   const bool gen = !is_pow2(g.M);
   if (rhs) {
@@ -1467,7 +1485,7 @@ static cudaError_t run_c2r(afid_ctx* c, const typename cplx<R>::T* spec,
   ProfScope ps(c, KF_C2R);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
-  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + g.M) * sizeof(typename cplx<R>::T);
+  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + g.M + g.M / 2 + 1) * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   const double scale = 1.0 / ((double)g.nx * (double)g.ny);
   const bool gen = !is_pow2(g.M);
