@@ -305,6 +305,8 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   const double* pa = flat.data() + offs[4];
   const double* pc = flat.data() + offs[5];
   const double* pdiag = flat.data() + offs[12];
+  c->hz = 0.0;
+  for (int k = 0; k < nz; ++k) c->hz += flat[offs[0] + k];  // the order the kernels summed in
 
   // ---- host tables
   std::vector<double2> twx(nx), twy(ny);

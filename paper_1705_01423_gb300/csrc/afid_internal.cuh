@@ -109,6 +109,7 @@ struct Grid {
 struct afid_ctx {
   afid::Grid g;
   double lx, ly;
+  double hz;  // sum of dzc over k = 0..nz-1 in that order (the wall-normal extent)
   int prec;
   double tol;
   int max_iter;

@@ -637,7 +637,9 @@ cudaError_t nusselt(afid_ctx* c, const double* w, const double* T, double coef, 
 // Reduction of the per-block partials of the first mixed-precision forward
 // transform (k_r2c_x32<R32_FIRST>): weighted mean of b and ||b - mean||^2;
 // resets the refinement's scalars.
-__global__ void k_bstats_final(Grid g, Metric m, const double* part, int np, double* scal) {
+// hz: sum of dzc (formed on the host: a serial loop of nz dependent FP64 adds
+// in one thread would cost the kernel more than its reduction).
+__global__ void k_bstats_final(Grid g, double hz, const double* part, int np, double* scal) {
   double sw = 0.0, s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) {
     sw += part[3 * i];
@@ -648,10 +650,8 @@ __global__ void k_bstats_final(Grid g, Metric m, const double* part, int np, dou
   s1 = block_sum(s1);
   s2 = block_sum(s2);
   if (threadIdx.x == 0) {
-    double swz = 0.0;
-    for (int k = 0; k < g.nz; ++k) swz += m.dzc[k];
     const double n = (double)g.nx * (double)g.ny * (double)g.nz;
-    const double mean = sw / (swz * (double)g.nx * (double)g.ny);
+    const double mean = sw / (hz * (double)g.nx * (double)g.ny);
     scal[S_BMEAN] = mean;
     scal[S_BNORM2] = s2 - 2.0 * mean * s1 + n * mean * mean;
     scal[S_RNORM2] = scal[S_BNORM2];
@@ -664,7 +664,7 @@ __global__ void k_bstats_final(Grid g, Metric m, const double* part, int np, dou
 
 cudaError_t bstats_final(afid_ctx* c) {
   ProfScope ps(c, KF_REFINE);
-  k_bstats_final<<<1, 1024, 0, c->stream>>>(c->g, c->m, c->part3, c2r_blocks(c->g), c->scal);
+  k_bstats_final<<<1, 1024, 0, c->stream>>>(c->g, c->hz, c->part3, c2r_blocks(c->g), c->scal);
   c->launches++;
   return cudaGetLastError();
 }
@@ -676,7 +676,7 @@ cudaError_t bstats_final(afid_ctx* c) {
 // under-estimates the error by up to the condition number of L.) Also records
 // the weighted mean of phi and the norm of the residual computed before this
 // correction.
-__global__ void k_refine_check(Grid g, Metric m, const double* part, int np, const double* part2,
+__global__ void k_refine_check(Grid g, double hz, const double* part, int np, const double* part2,
                                int np2, double* scal, double tol) {
   if (scal[S_CONVERGED] != 0.0) return;
   double d2 = 0.0, ps = 0.0, rs = 0.0;
@@ -691,11 +691,9 @@ __global__ void k_refine_check(Grid g, Metric m, const double* part, int np, con
   ps = block_sum(ps);
   rs = block_sum(rs);
   if (threadIdx.x == 0) {
-    double swz = 0.0;
-    for (int k = 0; k < g.nz; ++k) swz += m.dzc[k];
     // every accumulate pass removes the mean measured after the previous one
     // and sums dzc * delta_k: the weighted mean of phi is now that of delta_k
-    const double dm = ps / (swz * (double)g.nx * (double)g.ny);
+    const double dm = ps / (hz * (double)g.nx * (double)g.ny);
     scal[S_PHIMEAN] = dm;
     if (have_r) scal[S_RNORM2] = rs;
     scal[S_ITERS] += 1.0;
@@ -754,7 +752,7 @@ cudaError_t mixed_solve(afid_ctx* c, const double* b, double* phi, bool stats) {
   for (int it = 0; it < c->max_iter; ++it) {
     if ((e = spectral_solve_fp32(c, b, phi, phi, c->scal + S_CONVERGED, it, stats))) return e;
     ProfScope ps(c, KF_REFINE);
-    k_refine_check<<<1, 1024, 0, c->stream>>>(g, c->m, c->part3, np2, c->part2, np2, c->scal, c->tol);
+    k_refine_check<<<1, 1024, 0, c->stream>>>(g, c->hz, c->part3, np2, c->part2, np2, c->scal, c->tol);
     c->launches++;
     if ((e = cudaGetLastError())) return e;
   }
