@@ -144,12 +144,18 @@ class ClockSampler:
 def fft_ops(n: int) -> float:
     """FP64 operations per complex point of one n-point transform with the
     library's pass sequence (radix 8 first, untwiddled, then twiddled radix-8
-    passes, then one radix-4 or radix-2 pass): 6.5, 10, 7, 4 per point (a
+    passes, then one radix-4 or radix-2 pass): 6.5, 8.25, 7, 4 per point (a
     radix-8 butterfly is 52 operations with its 1/sqrt(2) scalings fused into
-    FMAs, a complex twiddle 4)."""
+    FMAs; the twiddled radix-8 passes take their seven twiddles in tangent form,
+    kappa (1 + i t), two FMAs each, the kappas folded into the butterfly's
+    additions: 66 per butterfly; a complex twiddle of the last radix-4 or
+    radix-2 pass 4). The tangent form is used for power-of-two lengths of at
+    least 64 (and at most 4096 in y); other lengths take 10 per twiddled
+    radix-8 pass."""
+    tangent = n >= 64 and n & (n - 1) == 0
     ops, p = 0.0, 1
     while n // p >= 8:
-        ops += 6.5 if p == 1 else 10.0
+        ops += 6.5 if p == 1 else (8.25 if tangent else 10.0)
         p *= 8
     if n // p == 4:
         ops += 7.0

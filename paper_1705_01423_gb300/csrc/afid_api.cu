@@ -147,7 +147,7 @@ size_t spec_elems(const afid_grid_desc* d) {
 }
 
 void free_all(afid_ctx* c) {
-  void* ps[] = {c->metric_buf, c->twx64, c->twy64, c->twx32, c->twy32, c->mtab64, c->mtab32,
+  void* ps[] = {c->metric_buf, c->twx64, c->twy64, c->ytan64[0], c->ytan64[1], c->xtan64[0], c->xtan64[1], c->twx32, c->twy32, c->mtab64, c->mtab32,
                 c->lamx, c->lamy, c->spec, c->phi, c->bbuf, c->R[0], c->R[1], c->R[2],
                 c->R[3], c->cntab, c->pa32, c->pc32, c->lowslot, c->low_modes, c->low_scratch, c->scal, c->mtabt32,
                 c->part, c->part2, c->part3, c->rres, c->dprev, c->cff, c->stat_buf};
@@ -347,6 +347,20 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   c->metric_buf = A.get<double>(flat.size());
   c->twx64 = A.get<double2>(nx);
   c->twy64 = A.get<double2>(ny);
+  // tangent-form tables of the FP64 y transform (power-of-two ny >= 64)
+  // (the tile of the y kernel then has at most 512 threads: ny <= 4096)
+  const bool ytan = ny >= 64 && ny <= 4096 && (ny & (ny - 1)) == 0;
+  c->ytan_len = ytan ? tan_tables(ny, nullptr, false, nullptr) : 0;
+  if (ytan) {
+    c->ytan64[0] = A.get<double>(c->ytan_len);
+    c->ytan64[1] = A.get<double>(c->ytan_len);
+  }
+  const bool xtan = M >= 64 && (M & (M - 1)) == 0;
+  c->xtan_len = xtan ? tan_tables(M, nullptr, false, nullptr) : 0;
+  if (xtan) {
+    c->xtan64[0] = A.get<double>(c->xtan_len);
+    c->xtan64[1] = A.get<double>(c->xtan_len);
+  }
   c->twx32 = A.get<float2>(nx);
   c->twy32 = A.get<float2>(ny);
   c->lamx = A.get<double>(M + 1);
@@ -401,6 +415,22 @@ afid_status afid_create(const afid_grid_desc* desc, const afid_phys* phys, void*
   up(c->metric_buf, flat.data(), flat.size() * sizeof(double));
   up(c->twx64, twx.data(), nx * sizeof(double2));
   up(c->twy64, twy.data(), ny * sizeof(double2));
+  if (c->ytan_len > 0) {
+    std::vector<double> tt(c->ytan_len);
+    for (int d = 0; d < 2; ++d) {
+      tan_tables(ny, twy.data(), d == 1, tt.data());
+      up(c->ytan64[d], tt.data(), tt.size() * sizeof(double));
+    }
+  }
+  if (c->xtan_len > 0) {
+    std::vector<double2> twm(M);  // exp(-2 pi i m/M) = the x table at even indices
+    for (int q = 0; q < M; ++q) twm[q] = twx[2 * q];
+    std::vector<double> tt(c->xtan_len);
+    for (int d = 0; d < 2; ++d) {
+      tan_tables(M, twm.data(), d == 1, tt.data());
+      up(c->xtan64[d], tt.data(), tt.size() * sizeof(double));
+    }
+  }
   up(c->twx32, twx32.data(), nx * sizeof(float2));
   up(c->twy32, twy32.data(), ny * sizeof(float2));
   up(c->lamx, lamx.data(), (M + 1) * sizeof(double));

@@ -125,6 +125,15 @@ struct afid_ctx {
   // twiddle tables exp(-2 pi i m / N): x table of nx entries, y table of ny entries
   double2 *twx64, *twy64;
   float2 *twx32, *twy32;
+  // FP64 y transform, power-of-two ny >= 64: tangent-form twiddle tables
+  // (tan_tables), forward [0] and inverse [1], ytan_len doubles each; null
+  // otherwise (the plain twiddles are used)
+  double* ytan64[2];
+  int ytan_len;
+  // FP64 x transforms, power-of-two M = nx/2 >= 64: the same for the M-point
+  // FFT (twiddles exp(-2 pi i m/M))
+  double* xtan64[2];
+  int xtan_len;
   // Thomas factor tables mtab[k][kyh][kx] (kyh = min(ky, ny-ky)); mtab64 always,
   // mtab32 in mixed mode; low-mode mask threshold for mixed mode
   double* mtab64;
@@ -213,6 +222,7 @@ cudaError_t run_fft_y_tma(afid_ctx* c, const typename cplx<R>::T* tw, bool inv, 
 // s is read from the device scalar S_PROJ_S when `dev_s`, else 1.
 cudaError_t spectral_solve(afid_ctx* c, const double* rhs, const double* u, const double* v,
                            const double* w, bool dev_s, double* phi, bool want_stats);
+int tan_tables(int N, const double2* tw, bool inv, double* out);  // host; k_spectral.cu
 int c2r_blocks(const Grid& g);
 // Fused small-nz kernel (mixed): shared memory (lmax: most low modes in one
 // kx column) and threads per block.

@@ -306,6 +306,121 @@ __device__ __forceinline__ void fft_line_pt_ix(C* buf, int N, const C* tabs, int
   else if (n2 == 2) stockham_pass_ix<2, INV, C, IX, true>(buf, N, p, tabs + off, 1, t, active, ix);
 }
 
+// FP64 radix-8 pass of span p > 1 with its twiddles in tangent form. The
+// twiddle W_r = exp(+-2 pi i r k / (8p)) of input r is written kappa_r (1 + i t_r)
+// with |t_r| <= 1: kappa_r = cos, t_r = tan where |cos| >= |sin|; elsewhere the
+// input is first rotated by i (exact: a swap and a sign) and W_r / i =
+// sin (1 - i cot), kappa_r = sin, t_r = -cot. The product costs two FMAs instead
+// of four; the seven factors kappa_r go into the butterfly's own additions,
+// which become FMAs (kappa_4 and kappa_2 into the even 4-point DFT, ratios
+// kappa_6/kappa_2, kappa_5/kappa_1, kappa_7/kappa_3, kappa_3/kappa_1 inside
+// it, kappa_1 and kappa_1/sqrt2 into the final combination): 66 FP64
+// operations per butterfly of 8 points instead of 80, the same DFT (the
+// arithmetic order differs, the results agree to rounding). `tab` is this
+// pass's table, 16 rows of p doubles ([row][k]): rows 0..6 t_1..t_7, 7 kappa_4,
+// 8 kappa_6/kappa_2, 9 kappa_2, 10 kappa_5/kappa_1, 11 kappa_7/kappa_3,
+// 12 kappa_3/kappa_1, 13 kappa_1, 14 kappa_1/sqrt2, 15 the rotated inputs as
+// a bit mask (bit r) in the bits of a double. Forward and inverse passes take
+// their own tables. Built by tan_tables (host).
+template <bool INV, typename IX>
+__device__ __forceinline__ void stockham_pass8_tan(double2* buf, int N, int p, const double* tab, int t,
+                                                   bool active, IX ix) {
+  double2 x[8];
+  const int nb = N / 8;
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) x[r] = buf[ix(t + r * nb)];
+  }
+  __syncthreads();
+  if (active) {
+    const int k = t & (p - 1);
+    const unsigned long long fl = (unsigned long long)__double_as_longlong(tab[15 * p + k]);
+    // z_r: input r times (1 + i t_r), after the rotation by i where flagged
+    auto tw = [&](int r) {
+      const double tr = tab[(r - 1) * p + k];
+      const bool rot = (fl >> r) & 1ull;
+      // (a, b) = i x where rotated (integer sign flip and selects), else x
+      const double nyv = __longlong_as_double(__double_as_longlong(x[r].y) ^ (long long)0x8000000000000000ull);
+      const double a = rot ? nyv : x[r].x;
+      const double b = rot ? x[r].x : x[r].y;
+      return double2{fma(-tr, b, a), fma(tr, a, b)};
+    };
+    // even 4-point DFT of (x0, kappa_2 z2, kappa_4 z4, kappa_6 z6), formed
+    // before the odd inputs are touched (fewer live registers)
+    double2 e0, e1, e2, e3;
+    {
+      const double2 z2 = tw(2), z4 = tw(4), z6 = tw(6);
+      const double k4 = tab[7 * p + k], r26 = tab[8 * p + k], k2 = tab[9 * p + k];
+      const double2 t0{fma(k4, z4.x, x[0].x), fma(k4, z4.y, x[0].y)};
+      const double2 t1{fma(-k4, z4.x, x[0].x), fma(-k4, z4.y, x[0].y)};
+      const double2 t2{fma(r26, z6.x, z2.x), fma(r26, z6.y, z2.y)};
+      const double2 t3 = rot_mi<INV>(double2{fma(-r26, z6.x, z2.x), fma(-r26, z6.y, z2.y)});
+      e0 = double2{fma(k2, t2.x, t0.x), fma(k2, t2.y, t0.y)};
+      e2 = double2{fma(-k2, t2.x, t0.x), fma(-k2, t2.y, t0.y)};
+      e1 = double2{fma(k2, t3.x, t1.x), fma(k2, t3.y, t1.y)};
+      e3 = double2{fma(-k2, t3.x, t1.x), fma(-k2, t3.y, t1.y)};
+    }
+    // odd 4-point DFT of (kappa_1 z1, kappa_3 z3, kappa_5 z5, kappa_7 z7), kappa_1 factored out
+    double2 o0, o1, o2, o3;
+    {
+      const double2 z1 = tw(1), z3 = tw(3), z5 = tw(5), z7 = tw(7);
+      const double r15 = tab[10 * p + k], r37 = tab[11 * p + k], r13 = tab[12 * p + k];
+      const double2 u0{fma(r15, z5.x, z1.x), fma(r15, z5.y, z1.y)};
+      const double2 u1{fma(-r15, z5.x, z1.x), fma(-r15, z5.y, z1.y)};
+      const double2 u2{fma(r37, z7.x, z3.x), fma(r37, z7.y, z3.y)};
+      const double2 u3 = rot_mi<INV>(double2{fma(-r37, z7.x, z3.x), fma(-r37, z7.y, z3.y)});
+      o0 = double2{fma(r13, u2.x, u0.x), fma(r13, u2.y, u0.y)};
+      o2 = double2{fma(-r13, u2.x, u0.x), fma(-r13, u2.y, u0.y)};
+      o1 = double2{fma(r13, u3.x, u1.x), fma(r13, u3.y, u1.y)};
+      o3 = double2{fma(-r13, u3.x, u1.x), fma(-r13, u3.y, u1.y)};
+    }
+    // w8 twiddles of the odd outputs (the 1/sqrt2 is in hk1), as in dft8
+    if (!INV) {
+      o1 = double2{o1.x + o1.y, o1.y - o1.x};
+      o3 = double2{o3.y - o3.x, -(o3.x + o3.y)};
+    } else {
+      o1 = double2{o1.x - o1.y, o1.x + o1.y};
+      o3 = double2{-(o3.x + o3.y), o3.x - o3.y};
+    }
+    const double2 q2 = rot_mi<INV>(o2);
+    const double k1 = tab[13 * p + k], hk1 = tab[14 * p + k];
+    double2 y[8];
+    y[0] = double2{fma(k1, o0.x, e0.x), fma(k1, o0.y, e0.y)};
+    y[4] = double2{fma(-k1, o0.x, e0.x), fma(-k1, o0.y, e0.y)};
+    y[1] = double2{fma(hk1, o1.x, e1.x), fma(hk1, o1.y, e1.y)};
+    y[5] = double2{fma(-hk1, o1.x, e1.x), fma(-hk1, o1.y, e1.y)};
+    y[2] = double2{fma(k1, q2.x, e2.x), fma(k1, q2.y, e2.y)};
+    y[6] = double2{fma(-k1, q2.x, e2.x), fma(-k1, q2.y, e2.y)};
+    y[3] = double2{fma(hk1, o3.x, e3.x), fma(hk1, o3.y, e3.y)};
+    y[7] = double2{fma(-hk1, o3.x, e3.x), fma(-hk1, o3.y, e3.y)};
+    const int o = (t - k) * 8 + k;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) buf[ix(o + r * p)] = y[r];
+  }
+  __syncthreads();
+}
+
+// Transform of a power-of-two line of N >= 64 FP64 points with the radix-8
+// passes of span p > 1 in tangent form: the first pass (no twiddles) as in
+// fft_line, then stockham_pass8_tan per radix-8 pass, then a last radix-4 or
+// radix-2 pass with its per-pass table of pass_twiddles (complex) after the
+// tangent tables. Layout: tan_tables (host).
+template <bool INV, typename IX>
+__device__ __forceinline__ void fft_line_tan_ix(double2* buf, int N, const double* tab, int t, bool active,
+                                                IX ix) {
+  stockham_pass_ix<8, INV>(buf, N, 1, reinterpret_cast<const double2*>(tab), 1, t, active, ix);
+  int p = 8, n2 = N / 8, off = 0;
+  while (n2 >= 8) {
+    stockham_pass8_tan<INV>(buf, N, p, tab + off, t, active, ix);
+    off += 16 * p;
+    p *= 8;
+    n2 /= 8;
+  }
+  const double2* tw2 = reinterpret_cast<const double2*>(tab + off);
+  if (n2 == 4) stockham_pass_ix<4, INV, double2, IX, true>(buf, N, p, tw2, 1, t, active, ix);
+  else if (n2 == 2) stockham_pass_ix<2, INV, double2, IX, true>(buf, N, p, tw2, 1, t, active, ix);
+}
+
 template <bool INV, typename C>
 __device__ __forceinline__ void fft_line_pt(C* buf, int N, const C* tabs, int t, bool active) {
   fft_line_pt_ix<INV, 0>(buf, N, tabs, t, active, PadIx{});

@@ -9,6 +9,10 @@
 // system per thread with threads along kx, so every global access is coalesced
 // and no global transpose is ever made (the paper's pencil transposes become
 // this choice of layout).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
 #include "afid_internal.cuh"
 
 namespace afid {
@@ -154,15 +158,19 @@ template <> __device__ __forceinline__ float to_real<float>(double x) {
   return __uint_as_float(sign | ((unsigned)e << 23) | mant);
 }
 
-template <typename R, int MODE, bool GEN>
-__global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* __restrict__ src,
+// TAN (FP64, power-of-two M >= 64): the M-point FFT's radix-8 passes take their
+// twiddles in tangent form from `ttab` (tan_tables, forward, tlen doubles),
+// copied over the per-pass table region.
+template <typename R, int MODE, bool GEN, bool TAN = false>
+__global__ void __launch_bounds__(512, TAN ? 2 : 0) k_r2c_x(Grid g, Metric m, const double* __restrict__ src,
                                                const double* __restrict__ u,
                                                const double* __restrict__ v,
                                                const double* __restrict__ w, double scale,
                                                typename cplx<R>::T* __restrict__ spec,
                                                const typename cplx<R>::T* __restrict__ tw,
                                                double* scal, int want_stats,
-                                               const double* __restrict__ skip, int dev_s) {
+                                               const double* __restrict__ skip, int dev_s,
+                                               const double* __restrict__ ttab, int tlen) {
   using C = typename cplx<R>::T;
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -178,9 +186,14 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
   C* buf = sm + line * stride;
   C* stw = sm + lines * stride;  // twiddle table, nx entries
   C* stp = stw + g.nx;           // per-pass tables of the M-point FFT (power-of-two M)
-  C* stq = stp + M;              // unpacking twiddles w_k / 2, k <= M/2
+  C* stq = stp + (TAN ? max(M, (tlen + 1) / 2) : M);  // unpacking twiddles w_k / 2, k <= M/2
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
-  if (!GEN) pass_twiddles(stp, tw, M, 2, threadIdx.x, blockDim.x);
+  if constexpr (TAN) {
+    double* sd = reinterpret_cast<double*>(stp);
+    for (int q = threadIdx.x; q < tlen; q += blockDim.x) sd[q] = ttab[q];
+  } else if (!GEN) {
+    pass_twiddles(stp, tw, M, 2, threadIdx.x, blockDim.x);
+  }
   for (int q = threadIdx.x; q <= M / 2; q += blockDim.x) stq[q] = cscale(tw[q], (R)0.5);
   double amax = 0.0;
   if (active) {
@@ -223,6 +236,8 @@ __global__ void __launch_bounds__(512) k_r2c_x(Grid g, Metric m, const double* _
   }
   __syncthreads();
   if constexpr (GEN) fft_line<false, true>(buf, M, stw, 2, t, active);
+  else if constexpr (TAN)  // launched for FP64 lines only (the cast is the identity there)
+    fft_line_tan_ix<false>(reinterpret_cast<double2*>(buf), M, reinterpret_cast<const double*>(stp), t, active, PadIx{});
   else fft_line_pt<false>(buf, M, stp, t, active);
   if (active) {
     C* out = spec + (size_t)row * g.P;
@@ -583,15 +598,17 @@ __global__ void __launch_bounds__(MODE == R32_RESUPD_ST ? 256 : 512, MODE == R32
 //   MODE 2 writes phi = delta (the first correction);
 //   MODE 1 adds phi += delta - mean_W(phi) (the mean measured after the
 //   previous correction), so that the gauge of phi is kept as it is refined.
-template <typename R, int MODE, bool GEN>
-__global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
+// TAN: as in k_r2c_x, with the inverse tables.
+template <typename R, int MODE, bool GEN, bool TAN = false>
+__global__ void __launch_bounds__(512, TAN ? 2 : 0) k_c2r_x(Grid g, Metric m,
                                                const typename cplx<R>::T* __restrict__ spec,
                                                const typename cplx<R>::T* __restrict__ tw,
                                                double scale, double* __restrict__ phi,
                                                const double* __restrict__ skip,
                                                double* __restrict__ part,
                                                const double* __restrict__ pmean,
-                                               float* __restrict__ dprev) {
+                                               float* __restrict__ dprev,
+                                               const double* __restrict__ ttab, int tlen) {
   using C = typename cplx<R>::T;
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -606,9 +623,14 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
   C* buf = sm + line * stride;
   C* stw = sm + lines * stride;  // twiddle table, nx entries
   C* stp = stw + g.nx;           // per-pass tables of the M-point FFT (power-of-two M)
-  C* stq = stp + M;              // MODE 0: packing twiddles scale * w_k, k <= M/2
+  C* stq = stp + (TAN ? max(M, (tlen + 1) / 2) : M);  // MODE 0: packing twiddles scale * w_k, k <= M/2
   for (int q = threadIdx.x; q < g.nx; q += blockDim.x) stw[q] = tw[q];
-  if (!GEN) pass_twiddles(stp, tw, M, 2, threadIdx.x, blockDim.x);
+  if constexpr (TAN) {
+    double* sd = reinterpret_cast<double*>(stp);
+    for (int q = threadIdx.x; q < tlen; q += blockDim.x) sd[q] = ttab[q];
+  } else if (!GEN) {
+    pass_twiddles(stp, tw, M, 2, threadIdx.x, blockDim.x);
+  }
   if (MODE == 0)
     for (int q = threadIdx.x; q <= M / 2; q += blockDim.x) stq[q] = cscale(tw[q], (R)scale);
   if (active) {
@@ -647,6 +669,8 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
   C zr[8];
   if constexpr (REGS) fft_line_pow2_to_regs<true, true>(buf, M, zr, stp, 2, t, active);
   else if constexpr (GEN) fft_line<true, true>(buf, M, stw, 2, t, active);
+  else if constexpr (TAN)  // launched for FP64 lines only (the cast is the identity there)
+    fft_line_tan_ix<true>(reinterpret_cast<double2*>(buf), M, reinterpret_cast<const double*>(stp), t, active, PadIx{});
   else fft_line_pt<true>(buf, M, stp, t, active);
   R d2 = (R)0, dsum = (R)0, dcomp = (R)0;
   double psum = 0.0;
@@ -704,10 +728,14 @@ __global__ void __launch_bounds__(512) k_c2r_x(Grid g, Metric m,
 
 // --------------------------------------------------------------------------
 // Complex FFT along y for a tile of TK consecutive kx columns of one z plane.
-template <typename R, bool INV, int TK, bool GEN>
+// TAN (FP64, power-of-two ny >= 64): the radix-8 passes with their twiddles in
+// tangent form (stockham_pass8_tan), `ttab` the direction's tables of
+// tan_tables, `tlen` doubles; otherwise the twiddles come from `tw`.
+template <typename R, bool INV, int TK, bool GEN, bool TAN = false>
 __global__ void __launch_bounds__(1024) k_fft_y(Grid g, typename cplx<R>::T* __restrict__ spec,
                                                 const typename cplx<R>::T* __restrict__ tw,
-                                                const double* __restrict__ skip) {
+                                                const double* __restrict__ skip,
+                                                const double* __restrict__ ttab = nullptr, int tlen = 0) {
   using C = typename cplx<R>::T;
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -717,8 +745,13 @@ __global__ void __launch_bounds__(1024) k_fft_y(Grid g, typename cplx<R>::T* __r
   const int ncol = min(TK, g.M + 1 - kx0);
   const int line = threadIdx.x / T, t = threadIdx.x - line * T;
   const int stride = pad8(Ny) + 1;
-  C* stw = sm + TK * stride;  // twiddle table, ny entries
-  for (int q = threadIdx.x; q < Ny; q += blockDim.x) stw[q] = tw[q];
+  C* stw = sm + TK * stride;  // twiddle table, ny entries (TAN: the tangent tables)
+  if constexpr (TAN) {
+    double* st = reinterpret_cast<double*>(stw);
+    for (int q = threadIdx.x; q < tlen; q += blockDim.x) st[q] = ttab[q];
+  } else {
+    for (int q = threadIdx.x; q < Ny; q += blockDim.x) stw[q] = tw[q];
+  }
   C* base = spec + (size_t)z * Ny * g.P + kx0;
   // Ny * TK = 8 * blockDim.x: eight independent loads per thread, all in flight
   C vals[8];
@@ -735,7 +768,10 @@ __global__ void __launch_bounds__(1024) k_fft_y(Grid g, typename cplx<R>::T* __r
     if (c < ncol) sm[c * stride + pad8(ky)] = vals[q];
   }
   __syncthreads();
-  fft_line<INV, GEN>(sm + line * stride, Ny, stw, 1, t, line < ncol);
+  if constexpr (TAN)
+    fft_line_tan_ix<INV>(sm + line * stride, Ny, reinterpret_cast<const double*>(stw), t, line < ncol, PadIx{});
+  else
+    fft_line<INV, GEN>(sm + line * stride, Ny, stw, 1, t, line < ncol);
   for (int e = threadIdx.x; e < Ny * TK; e += blockDim.x) {
     const int ky = e / TK, c = e - (e / TK) * TK;
     if (c < ncol) base[(size_t)ky * g.P + c] = sm[c * stride + pad8(ky)];
@@ -1432,14 +1468,35 @@ static cudaError_t run_fft_y(afid_ctx* c, typename cplx<R>::T* spec, const typen
   while (tk > 1 && ((size_t)tk * ls > 112 * 1024 || tk * (g.ny / 8) > 1024)) tk /= 2;
   dim3 grd(ceil_div(g.M + 1, tk), g.nz);
   const int thr = tk * (g.ny / 8);
-  const size_t sm = (size_t)tk * ls + (size_t)g.ny * sizeof(typename cplx<R>::T);
   const bool gen = !is_pow2(g.ny);  // radix-3/5 passes needed
+  if constexpr (sizeof(R) == sizeof(double)) {
+    if (c->ytan64[0]) {  // tangent-form twiddles (power-of-two ny >= 64)
+      const size_t sm = (size_t)tk * ls + (size_t)c->ytan_len * sizeof(double);
+      const double* tt = c->ytan64[inv ? 1 : 0];
+#define AFID_FFTYT(TKV)                                                                         \
+  do {                                                                                          \
+    auto kf = inv ? k_fft_y<double, true, TKV, false, true> : k_fft_y<double, false, TKV, false, true>; \
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
+    kf<<<grd, thr, sm, c->stream>>>(g, spec, tw, skip, tt, c->ytan_len);                        \
+  } while (0)
+      switch (tk) {
+        case 8: AFID_FFTYT(8); break;
+        case 4: AFID_FFTYT(4); break;
+        case 2: AFID_FFTYT(2); break;
+        default: AFID_FFTYT(1); break;
+      }
+#undef AFID_FFTYT
+      c->launches++;
+      return cudaGetLastError();
+    }
+  }
+  const size_t sm = (size_t)tk * ls + (size_t)g.ny * sizeof(typename cplx<R>::T);
 #define AFID_FFTY(TKV)                                                                        \
   do {                                                                                        \
     auto kf = inv ? (gen ? k_fft_y<R, true, TKV, true> : k_fft_y<R, true, TKV, false>)       \
                   : (gen ? k_fft_y<R, false, TKV, true> : k_fft_y<R, false, TKV, false>);    \
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);           \
-    kf<<<grd, thr, sm, c->stream>>>(g, spec, tw, skip);                                      \
+    kf<<<grd, thr, sm, c->stream>>>(g, spec, tw, skip, nullptr, 0);                                    \
   } while (0)
   switch (tk) {
     case 8: AFID_FFTY(8); break;
@@ -1460,19 +1517,24 @@ static cudaError_t run_r2c(afid_ctx* c, const double* rhs, const double* u, cons
   ProfScope ps(c, KF_R2C);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
-  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + g.M + g.M / 2 + 1) * sizeof(typename cplx<R>::T);
+  // tangent-form twiddles for the FP64 transform where the context has them
+  const bool tan = sizeof(R) == sizeof(double) && c->xtan64[0] != nullptr;
+  const int tlen = tan ? c->xtan_len : 0;
+  const int tabw = tan ? std::max(g.M, (tlen + 1) / 2) : g.M;
+  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + tabw + g.M / 2 + 1) * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   const bool gen = !is_pow2(g.M);
+  const double* tt = tan ? c->xtan64[0] : nullptr;
   if (rhs) {
-    auto kf = gen ? k_r2c_x<R, MODE_RHS, true> : k_r2c_x<R, MODE_RHS, false>;
+    auto kf = gen ? k_r2c_x<R, MODE_RHS, true> : (tan ? k_r2c_x<R, MODE_RHS, false, true> : k_r2c_x<R, MODE_RHS, false>);
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, rhs, u, v, w, scale, spec, tw, c->scal,
-                                             want_stats, skip, (int)dev_s);
+                                             want_stats, skip, (int)dev_s, tt, tlen);
   } else {
-    auto kf = gen ? k_r2c_x<R, MODE_DIV, true> : k_r2c_x<R, MODE_DIV, false>;
+    auto kf = gen ? k_r2c_x<R, MODE_DIV, true> : (tan ? k_r2c_x<R, MODE_DIV, false, true> : k_r2c_x<R, MODE_DIV, false>);
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, rhs, u, v, w, scale, spec, tw, c->scal,
-                                             want_stats, skip, (int)dev_s);
+                                             want_stats, skip, (int)dev_s, tt, tlen);
   }
   c->launches++;
   return cudaGetLastError();
@@ -1485,15 +1547,21 @@ static cudaError_t run_c2r(afid_ctx* c, const typename cplx<R>::T* spec,
   ProfScope ps(c, KF_C2R);
   const Grid& g = c->g;
   const int T = g.M / 8, lines = r2c_lines<R>(g);
-  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + g.M + g.M / 2 + 1) * sizeof(typename cplx<R>::T);
+  // tangent-form twiddles for the FP64 transform where the context has them
+  const bool tan = sizeof(R) == sizeof(double) && c->xtan64[1] != nullptr;
+  const int tlen = tan ? c->xtan_len : 0;
+  const int tabw = tan ? std::max(g.M, (tlen + 1) / 2) : g.M;
+  const size_t sm = (size_t)lines * line_smem<R>(g.M) + (size_t)(g.nx + tabw + g.M / 2 + 1) * sizeof(typename cplx<R>::T);
   const int blocks = ceil_div((long long)g.nz * g.ny, lines);
   const double scale = 1.0 / ((double)g.nx * (double)g.ny);
   const bool gen = !is_pow2(g.M);
   auto kf = gen ? (mode == 1 ? k_c2r_x<R, 1, true> : (mode == 2 ? k_c2r_x<R, 2, true> : k_c2r_x<R, 0, true>))
-                : (mode == 1 ? k_c2r_x<R, 1, false> : (mode == 2 ? k_c2r_x<R, 2, false> : k_c2r_x<R, 0, false>));
+                : (mode == 1 ? k_c2r_x<R, 1, false>
+                             : (mode == 2 ? k_c2r_x<R, 2, false> : (tan ? k_c2r_x<R, 0, false, true> : k_c2r_x<R, 0, false>)));
   cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   kf<<<blocks, lines * T, sm, c->stream>>>(g, c->m, spec, tw, scale, phi, skip, part, c->scal + S_PHIMEAN,
-                                           sizeof(R) == sizeof(float) ? c->dprev : nullptr);
+                                           sizeof(R) == sizeof(float) ? c->dprev : nullptr,
+                                           tan ? c->xtan64[1] : nullptr, tlen);
   c->launches++;
   return cudaGetLastError();
 }
@@ -1611,6 +1679,65 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_
   if ((e = cudaGetLastError())) return e;
   if ((e = run_fft_y<float>(c, spec, c->twy32, true, skip))) return e;
   return run_c2r<float>(c, spec, c->twx32, phi, first ? 2 : 1, skip, c->part2);
+}
+
+// Tables of fft_line_tan_ix for a power-of-two N >= 64 (host, FP64), in pass
+// order: per radix-8 pass of span p > 1, 16 rows of p doubles (layout in
+// stockham_pass8_tan), then for a last radix-4 or radix-2 pass its (R - 1) p
+// complex twiddles w = tw[r k N/(p R)] as pass_twiddles lays them out (the
+// inverse pass conjugates them itself). tw: exp(-2 pi i m/N), m < N. The
+// inverse tables take W = conj(w). Returns the length in doubles; out may be
+// null to size it.
+int tan_tables(int N, const double2* tw, bool inv, double* out) {
+  const double h = 0.70710678118654752440;  // the 1/sqrt2 of the radix-8 butterfly
+  int off = 0, p = 1, n2 = N;
+  while (n2 >= 8) {
+    if (p > 1) {
+      const int step = N / (8 * p);
+      for (int k = 0; out && k < p; ++k) {
+        double kap[8] = {1.0}, tt[8] = {0.0};
+        unsigned long long fl = 0;
+        for (int r = 1; r < 8; ++r) {
+          const double2 w = tw[r * k * step];
+          const double cs = w.x, sn = inv ? -w.y : w.y;
+          if (std::fabs(cs) >= std::fabs(sn)) {
+            kap[r] = cs;
+            tt[r] = sn / cs;
+          } else {  // W = i sin (1 - i cot): the input is rotated by i
+            kap[r] = sn;
+            tt[r] = -cs / sn;
+            fl |= 1ull << r;
+          }
+        }
+        for (int r = 1; r < 8; ++r) out[off + (r - 1) * p + k] = tt[r];
+        out[off + 7 * p + k] = kap[4];
+        out[off + 8 * p + k] = kap[6] / kap[2];
+        out[off + 9 * p + k] = kap[2];
+        out[off + 10 * p + k] = kap[5] / kap[1];
+        out[off + 11 * p + k] = kap[7] / kap[3];
+        out[off + 12 * p + k] = kap[3] / kap[1];
+        out[off + 13 * p + k] = kap[1];
+        out[off + 14 * p + k] = h * kap[1];
+        double flb;
+        std::memcpy(&flb, &fl, sizeof(flb));
+        out[off + 15 * p + k] = flb;
+      }
+      off += 16 * p;
+    }
+    p *= 8;
+    n2 /= 8;
+  }
+  if (n2 == 4 || n2 == 2) {
+    const int R = n2, step = N / (p * R);
+    for (int r = 1; out && r < R; ++r)
+      for (int k = 0; k < p; ++k) {
+        const double2 w = tw[r * k * step];
+        out[off + 2 * ((r - 1) * p + k)] = w.x;
+        out[off + 2 * ((r - 1) * p + k) + 1] = w.y;
+      }
+    off += 2 * (R - 1) * p;
+  }
+  return off;
 }
 
 int c2r_blocks(const Grid& g) {
