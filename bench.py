@@ -149,16 +149,17 @@ def fft_ops(n: int) -> float:
     FMAs; the twiddled radix-8 passes take their seven twiddles in tangent form,
     kappa (1 + i t), two FMAs each, the kappas folded into the butterfly's
     additions: 66 per butterfly; a complex twiddle of the last radix-4 or
-    radix-2 pass 4). The tangent form is used for power-of-two lengths of at
-    least 64 (and at most 4096 in y); other lengths take 10 per twiddled
-    radix-8 pass."""
+    radix-2 pass 4; the last radix-4 pass of a power-of-two length of at least
+    64 also takes the tangent form: 22 per butterfly, 5.5 per point). The
+    tangent form is used for power-of-two lengths of at least 64; other
+    lengths take 10 per twiddled radix-8 pass."""
     tangent = n >= 64 and n & (n - 1) == 0
     ops, p = 0.0, 1
     while n // p >= 8:
         ops += 6.5 if p == 1 else (8.25 if tangent else 10.0)
         p *= 8
     if n // p == 4:
-        ops += 7.0
+        ops += 5.5 if tangent else 7.0
     elif n // p == 2:
         ops += 4.0
     return ops

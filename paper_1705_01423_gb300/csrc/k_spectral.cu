@@ -1683,9 +1683,10 @@ cudaError_t spectral_solve_fp32(afid_ctx* c, const double* b, const double* phi_
 
 // Tables of fft_line_tan_ix for a power-of-two N >= 64 (host, FP64), in pass
 // order: per radix-8 pass of span p > 1, 16 rows of p doubles (layout in
-// stockham_pass8_tan), then for a last radix-4 or radix-2 pass its (R - 1) p
-// complex twiddles w = tw[r k N/(p R)] as pass_twiddles lays them out (the
-// inverse pass conjugates them itself). tw: exp(-2 pi i m/N), m < N. The
+// stockham_pass8_tan), then for a last radix-4 pass 7 rows of p doubles
+// (stockham_pass4_tan), or for a last radix-2 pass its p complex twiddles
+// w = tw[k N/(2p)] as pass_twiddles lays them out (the inverse pass conjugates
+// them itself). tw: exp(-2 pi i m/N), m < N. The
 // inverse tables take W = conj(w). Returns the length in doubles; out may be
 // null to size it.
 int tan_tables(int N, const double2* tw, bool inv, double* out) {
@@ -1727,7 +1728,33 @@ int tan_tables(int N, const double2* tw, bool inv, double* out) {
     p *= 8;
     n2 /= 8;
   }
-  if (n2 == 4 || n2 == 2) {
+  if (n2 == 4) {  // last radix-4 pass in tangent form: 7 rows of p (stockham_pass4_tan)
+    const int step = N / (4 * p);
+    for (int k = 0; out && k < p; ++k) {
+      double kap[4] = {1.0}, tt[4] = {0.0};
+      unsigned long long fl = 0;
+      for (int r = 1; r < 4; ++r) {
+        const double2 w = tw[r * k * step];
+        const double cs = w.x, sn = inv ? -w.y : w.y;
+        if (std::fabs(cs) >= std::fabs(sn)) {
+          kap[r] = cs;
+          tt[r] = sn / cs;
+        } else {
+          kap[r] = sn;
+          tt[r] = -cs / sn;
+          fl |= 1ull << r;
+        }
+      }
+      for (int r = 1; r < 4; ++r) out[off + (r - 1) * p + k] = tt[r];
+      out[off + 3 * p + k] = kap[2];
+      out[off + 4 * p + k] = kap[3] / kap[1];
+      out[off + 5 * p + k] = kap[1];
+      double flb;
+      std::memcpy(&flb, &fl, sizeof(flb));
+      out[off + 6 * p + k] = flb;
+    }
+    off += 7 * p;
+  } else if (n2 == 2) {
     const int R = n2, step = N / (p * R);
     for (int r = 1; out && r < R; ++r)
       for (int k = 0; k < p; ++k) {

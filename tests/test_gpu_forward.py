@@ -48,6 +48,24 @@ def test_poisson_fp64(shape):
     assert abs(info["rhs_absmax"] - float(np.abs(b).max())) < 1e-15 * float(np.abs(b).max())
 
 
+# Pass structures of the FP64 transforms with tangent-form twiddles (power-of-two
+# lengths >= 64): x lengths nx/2 = 256 (radix 8, 8, 4) and 512 (8, 8, 8); y lengths
+# 256 (8, 8, 4), 1024 (8, 8, 8, 2: a plain radix-2 last pass), 2048 (8, 8, 8, 4) and
+# 4096 (four radix-8 passes, the largest ny a context takes).
+TANGENT_SHAPES = [(512, 16, 6), (1024, 8, 4), (16, 256, 6), (16, 1024, 4), (16, 2048, 3), (16, 4096, 3)]
+
+
+@pytest.mark.parametrize("shape", TANGENT_SHAPES)
+def test_poisson_fp64_tangent_twiddle_passes(shape):
+    nx, ny, nz = shape
+    w = synth.workload("pc64", nx=nx, ny=ny, nz=nz, lx=2.0, ly=1.3)
+    g = ogrid(w)
+    b = synth.noise(g.cell_shape(), seed=nx + ny + nz)
+    ref = poisson.solve(g, cpu(b))
+    phi = make_ctx(w, poisson_only=True).poisson_solve(gpu(b))
+    assert rel_l2(phi, ref) < TOL64
+
+
 def test_poisson_aliasing_and_repeat():
     w = synth.workload("pc64", nx=32, ny=32, nz=9)
     g = ogrid(w)
