@@ -181,7 +181,8 @@ def family_work(fam: str, w):
       FMA, the reciprocal pivot being folded into the right-hand side the
       explicit-terms kernel writes, and one back-substitution FMA each on the
       FP64 pipe; the q += dq addition is an atomic done in L2);
-      cfl_reduce 7 (|.| is an operand modifier)."""
+      cfl_reduce 6 (|.| is an operand modifier; the maximum is taken on the bit
+      patterns with integer instructions)."""
     nx, ny, nz = w.nx, w.ny, w.nz
     n = nx * ny * nz
     M1 = nx // 2 + 1
@@ -201,7 +202,7 @@ def family_work(fam: str, w):
     if fam == "crank_nicolson":
         return 4 * 24 * n, 8 * n
     if fam == "cfl_reduce":
-        return 24 * n, 7 * n
+        return 24 * n, 6 * n
     return None
 
 

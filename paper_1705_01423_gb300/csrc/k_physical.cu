@@ -20,6 +20,11 @@ template <typename T> __device__ __forceinline__ T warp_max(T v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+// integer maximum (ordered bit patterns of non-negative doubles)
+template <> __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -196,10 +201,13 @@ cudaError_t max_divergence(afid_ctx* c, const double* u, const double* v, const 
 
 // ---------------------------------------------------------------------------
 // CFL of Listing 1: 0.5 max(|u_i+u_i+1|/dx + |v_j+v_j+1|/dy + |w_k+w_k+1|/dzc_k),
-// floored at 1e-8; dt = min(cfl/cflm, dt_max).
+// floored at 1e-8; dt = min(cfl/cflm, dt_max). The terms are non-negative, so
+// their maximum is taken on the bit patterns with integer instructions (off the
+// FP64 pipe that bounds the kernel: 6 FP64 operations per point, not 7); a NaN
+// velocity gives a NaN CFL number.
 __global__ void k_cfl(Grid g, Metric m, const double* __restrict__ u, const double* __restrict__ v,
                       const double* __restrict__ w, unsigned long long* out) {
-  double mx = 0.0;
+  unsigned long long mx = 0ull;
   for (int row = blockIdx.x; row < g.nz * g.ny; row += gridDim.x) {
     const int k = row / g.ny, j = row - k * g.ny;
     const int jp = wrap_next(j, g.ny);
@@ -209,11 +217,11 @@ __global__ void k_cfl(Grid g, Metric m, const double* __restrict__ u, const doub
       const int ip = wrap_next(i, g.nx);
       const double q = fabs(u[c] + u[at(g, k, j, ip)]) * g.rdx + fabs(v[c] + v[at(g, k, jp, i)]) * g.rdy +
                        fabs(w[c] + w[c + (size_t)g.nx * g.ny]) * rz;
-      mx = fmax(mx, q);
+      mx = max(mx, dbl_key(q));
     }
   }
   mx = warp_max(mx);
-  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, dbl_key(mx));
+  if ((threadIdx.x & 31) == 0 && mx > 0ull) atomicMax(out, mx);
 }
 
 __global__ void k_cfl_final(double* scal, double cfl, double dt_max, double* cflm_dev) {
