@@ -786,35 +786,15 @@ __global__ void __launch_bounds__(1024) k_fft_y(Grid g, typename cplx<R>::T* __r
 // mixed precision the low modes (lambda < lam_thr) are left to k_thomas_low.
 // Forward elimination and back substitution of one column (rows k = 0..nz-1,
 // pa[0] = 0), with the loads of the next U rows issued together so that the
-// memory latency is paid once per U rows rather than once per row (FP32,
-// which is bound by memory latency; FP64 keeps the plain loop).
+// memory latency is paid once per U rows rather than once per row.
 template <typename R, typename C>
 __device__ __forceinline__ void thomas_column(C* __restrict__ col, const R* __restrict__ mt,
                                               const R* __restrict__ pa, const R* __restrict__ pc,
                                               int nz, size_t plane, size_t tplane) {
-  if constexpr (sizeof(R) == 8) {
-    // FP64: bound by the FP64 pipe; the plain loop keeps registers (and
-    // resident threads) for it
-    C dp = C{(R)0, (R)0};
-#pragma unroll 4
-    for (int k = 0; k < nz; ++k) {
-      const C d = col[k * plane];
-      const R mk = mt[k * tplane];
-      const R ak = pa[k];
-      dp = C{(d.x - ak * dp.x) * mk, (d.y - ak * dp.y) * mk};
-      col[k * plane] = dp;
-    }
-    C x = dp;
-#pragma unroll 4
-    for (int k = nz - 2; k >= 0; --k) {
-      const C e = col[k * plane];
-      const R cp = pc[k] * mt[k * tplane];
-      x = C{e.x - cp * x.x, e.y - cp * x.y};
-      col[k * plane] = x;
-    }
-    return;
-  }
-  constexpr int U = 8;
+  // rows loaded U at a time before they are used (the loads of a batch in
+  // flight together; a store to the column and the next row's load cannot be
+  // reordered by the compiler): 8 rows in FP32, 4 in FP64 (registers)
+  constexpr int U = sizeof(R) == 8 ? 4 : 8;
   C dv[U];
   R mv[U];
   C dp = C{(R)0, (R)0};
