@@ -175,7 +175,7 @@ def family_work(fam: str, w):
       c2r_x  packing 3 (the 1/(nx ny) normalisation folded in) + fft_ops(nx/2)/2
       fft_y  fft_ops(ny) per complex point (nx/2+1 complex per row)
       thomas 7 per complex point (4 forward, 3 backward)
-      project 9; rhs 104 (shared face fluxes 29, u 18, v 18, w 20, T 16, per-plane
+      project 9; rhs 104 (shared face fluxes 25, u 20, v 20, w 20, T 16, per-plane
       factors 3; the recomputed fluxes of the warp- and block-edge neighbours are
       overhead, not counted); crank_nicolson 8 (4 fields: one forward-elimination
       FMA, the reciprocal pivot being folded into the right-hand side the

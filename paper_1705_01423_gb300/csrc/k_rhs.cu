@@ -13,7 +13,12 @@
 //     double-buffered shared-memory exchange (one barrier per k).
 // Only the block's outer edges recompute a neighbour's flux (every lane of
 // the edge warp issues that code, since masked lanes cost the same issue
-// slots), so wider blocks spend fewer operations on edges.
+// slots), so wider blocks spend fewer operations on edges. The fluxes of u
+// through its x faces and of v through its y faces need no exchange at all:
+// their difference (u_i + u_i+1)^2 - (u_i-1 + u_i)^2 is formed as
+// (u_i+1 - u_i-1)(u_i+1 + u_i-1 + 2 u_i), whose sum the horizontal diffusion
+// needs anyway (the same operation count, and more accurate where the two
+// squares nearly cancel).
 // Constant factors (1/2, 1/4, 1/dx, dt gamma_l, ...) are folded; the
 // wall-normal term alpha_l dt d dzz q of R takes its three coefficients per
 // row from the substep's Crank-Nicolson table. The z-march of a column is
@@ -69,8 +74,7 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
   const int ip = wrap_next(i, nx), im = wrap_prev(i, nx);
   const int jp = wrap_next(j, ny), jm = wrap_prev(j, ny);
   const size_t NXY = (size_t)nx * ny;
-  const bool first_lane = tx == 0, last_lane = tx == BX - 1;
-  const bool first_row = ty == 0, last_row = ty == BY - 1;
+  const bool last_lane = tx == BX - 1, last_row = ty == BY - 1;
 
   // The right-hand sides are written multiplied by the reciprocal pivot m_k of
   // their Crank-Nicolson row (the sweep's forward elimination then needs no
@@ -91,10 +95,10 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
   const double qx = ph.qx, qy = ph.qy, hx = ph.hx, hy = ph.hy;
   const double nrx = ph.nrx, nry = ph.nry, nl0 = ph.nl0, krx = ph.krx, kry = ph.kry, kl0 = ph.kl0;
 
-  // shared y-exchange: [buffer][quantity][row][x]; x-edge exchange between
-  // the two warps of a row: fxw, fxt of x = 32 and fxu of x = 31
-  __shared__ double sx[2][4][BY][32 * WPR];
-  __shared__ double sxe[2][3][BY];
+  // shared y-exchange: [buffer][quantity][row][x] (C, fyw, fyt); x-edge
+  // exchange between the two warps of a row: fxw, fxt of x = 32
+  __shared__ double sx[2][3][BY][32 * WPR];
+  __shared__ double sxe[2][2][BY];
 
   const size_t col = (size_t)j * nx + i;
   const size_t cim = (size_t)j * nx + im, cip = (size_t)j * nx + ip;
@@ -141,8 +145,6 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
 
     // ---------------------------------------------------------------- shared fluxes (cell k)
     const double C = (vim + v0) * (ujm + u0);        // corner (x-face i, y-face j), x4
-    const double fxu = (u0 + uip) * (u0 + uip);       // u at cell centre i, x4
-    const double fyv = (v0 + vjp) * (v0 + vjp);       // v at cell centre j, x4
     const double fzu1 = k < nz - 1 ? (wk1im + wk1) * (u0 + ukp) : 0.0;  // face k+1, x4
     const double fzv1 = k < nz - 1 ? (wk1jm + wk1) * (v0 + vkp) : 0.0;
     const double wsum = w0 + wk1;                     // 2 w at cell centre k
@@ -171,30 +173,22 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
     }
     // ---------------------------------------------------------------- exchange
     sx[buf][0][ty][tx] = C;
-    sx[buf][1][ty][tx] = fyv;
-    sx[buf][2][ty][tx] = fyw;
-    sx[buf][3][ty][tx] = fyt;
-    if (WPR == 2) {
-      if (tx == 32) {
-        sxe[buf][0][ty] = fxw;
-        sxe[buf][1][ty] = fxt;
-      }
-      if (tx == 31) sxe[buf][2][ty] = fxu;
+    sx[buf][1][ty][tx] = fyw;
+    sx[buf][2][ty][tx] = fyt;
+    if (WPR == 2 && tx == 32) {
+      sxe[buf][0][ty] = fxw;
+      sxe[buf][1][ty] = fxt;
     }
     __syncthreads();
     // x neighbours by shuffle (lane i+1 / i-1 of the same row)
     const unsigned FULL = 0xffffffffu;
     double Cip = __shfl_down_sync(FULL, C, 1, SW);
-    double fxum = __shfl_up_sync(FULL, fxu, 1, SW);
     double fxw1 = __shfl_down_sync(FULL, fxw, 1, SW);
     double fxt1 = __shfl_down_sync(FULL, fxt, 1, SW);
-    if (WPR == 2) {  // facing edges of the two warps of a row
-      if (tx == 31) {
-        Cip = sx[buf][0][ty][32];
-        fxw1 = sxe[buf][0][ty];
-        fxt1 = sxe[buf][1][ty];
-      }
-      if (tx == 32) fxum = sxe[buf][2][ty];
+    if (WPR == 2 && tx == 31) {  // facing edges of the two warps of a row
+      Cip = sx[buf][0][ty][32];
+      fxw1 = sxe[buf][0][ty];
+      fxt1 = sxe[buf][1][ty];
     }
     // Block-edge lanes recompute the neighbour's fluxes. The warp-uniform
     // vote keeps these blocks a real branch taken only by the warps that
@@ -209,15 +203,11 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
         }
       }
     }
-    if (__any_sync(FULL, first_lane)) {
-      if (first_lane) fxum = (uim + u0) * (uim + u0);
-    }
     // y neighbours from shared memory (rows j+1 / j-1 of the block)
-    const int typ = last_row ? ty : ty + 1, tym = first_row ? ty : ty - 1;
+    const int typ = last_row ? ty : ty + 1;
     double Cjp = sx[buf][0][typ][tx];
-    double fyw1 = sx[buf][2][typ][tx];
-    double fyt1 = sx[buf][3][typ][tx];
-    double fyvm = sx[buf][1][tym][tx];
+    double fyw1 = sx[buf][1][typ][tx];
+    double fyt1 = sx[buf][2][typ][tx];
     if (__any_sync(FULL, last_row)) {
       if (last_row) {
         Cjp = (v[c + cjpim] + vjp) * (u0 + ujp);
@@ -230,15 +220,17 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
         }
       }
     }
-    if (__any_sync(FULL, first_row)) {
-      if (first_row) fyvm = (vjm + v0) * (vjm + v0);
-    }
 
     // ---------------------------------------------------------------- u, v at cell k
     const double qz = cnt[CN_QZ * L + k];  // dzc^-1 / 4
     {
-      const double A = fma(fzu1 - fzu, qz, fma(Cjp - C, qy, (fxu - fxum) * qx));
-      const double H = fma(nrx, uip + uim, fma(nry, ujp + ujm, fma(-nl0, u0, -A)));
+      // x flux difference (u_i + u_i+1)^2 - (u_i-1 + u_i)^2 as
+      // (u_i+1 - u_i-1)(u_i+1 + u_i-1 + 2 u_i), its sum shared with the diffusion:
+      // no neighbour's flux needed
+      const double sxu = uip + uim;
+      const double dfx = (uip - uim) * fma(2.0, u0, sxu);
+      const double A = fma(fzu1 - fzu, qz, fma(Cjp - C, qy, dfx * qx));
+      const double H = fma(nrx, sxu, fma(nry, ujp + ujm, fma(-nl0, u0, -A)));
       const double z = fma(cnt[CN_MEA * L + k], ukm, fma(cnt[CN_MEC * L + k], ukp, fma(cnt[CN_MED * L + k], u0, -cnt[CN_MGX * L + k] * (p0 - p[c + cim]))));
       double r = fma(cnt[CN_MCG * L + k], H, z);
       if (l > 0) r = fma(cnt[CN_MCR * L + k], Hu[c + col], r);
@@ -246,8 +238,10 @@ __global__ void __launch_bounds__(32 * WPR * BY, WPR * BY >= 16 ? 1 : 2) k_rhs_z
       Ru[c + col] = r;
     }
     {
-      const double A = fma(fzv1 - fzv, qz, fma(fyv - fyvm, qy, (Cip - C) * qx));
-      const double H = fma(nrx, vip + vim, fma(nry, vjp + vjm, fma(-nl0, v0, -A)));
+      const double syv = vjp + vjm;  // y flux difference of v, as for u in x
+      const double dfy = (vjp - vjm) * fma(2.0, v0, syv);
+      const double A = fma(fzv1 - fzv, qz, fma(dfy, qy, (Cip - C) * qx));
+      const double H = fma(nrx, vip + vim, fma(nry, syv, fma(-nl0, v0, -A)));
       const double z = fma(cnt[CN_MEA * L + k], vkm, fma(cnt[CN_MEC * L + k], vkp, fma(cnt[CN_MED * L + k], v0, -cnt[CN_MGY * L + k] * (p0 - p[c + cjm]))));
       double r = fma(cnt[CN_MCG * L + k], H, z);
       if (l > 0) r = fma(cnt[CN_MCR * L + k], Hv[c + col], r);
